@@ -1,0 +1,338 @@
+"""Benchmark of the PFAC scan (one JSON line on rank 0).
+
+A step is one pm_scan of the paper-scale workload: 20,000 byte patterns
+(lengths 8-64, half of them sharing a prefix with an earlier one) over a
+256 MiB uniform random text with one planted pattern per 64 KiB, text and
+outputs resident in HBM. The metric is Gbps of text scanned (8 * bytes /
+time), with the kernel's roofline fraction beside it.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Under torchrun each rank scans its own text (weak scaling, no data-path
+collective); the step time is the max over ranks. ``--impl reference`` times
+the CPU oracle on the host cores instead (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Gbps scanned & % roofline, batched/served vs plain PFAC (bit-exact); p99 ms"
+WORKLOAD = ("paper-scale plain PFAC: 20,000 patterns over bytes 0-255, lengths 8-64, "
+            "p=0.5 shared prefix with an earlier pattern; 256 MiB uniform text, "
+            "1 planted pattern per 64 KiB; seed 0")
+TEXT_BYTES = 256 * 1024 * 1024
+N_PATTERNS = 20000
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ----------------------------------------------------------------------------
+# clocks during the timed region
+
+
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for name, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": mx, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------
+
+
+def kernel_source_sha():
+    h = hashlib.sha256()
+    for f in ("pm_scan.cu", "pm_internal.h"):
+        with open(os.path.join(ROOT, "paper_1702_03657_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def profiled_traffic():
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", "pfac_scan_paper_scale.md")
+    try:
+        txt = open(path).read()
+    except OSError:
+        return None
+    m1 = re.search(r"kernel_source_sha256:\s*([0-9a-f]{64})", txt)
+    m2 = re.search(r"dram_bytes_per_launch_full_size:\s*([0-9.eE+]+)", txt)
+    if not (m1 and m2) or m1.group(1) != kernel_source_sha():
+        return None
+    return float(m2.group(1))
+
+
+def measured_peak_hbm():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def cpu_baseline(wl, seconds: float):
+    """The oracle's PFAC walk, as it stands, on the host cores, over a
+    bounded contiguous sample of the same text."""
+    import oracle
+    cores = os.cpu_count() or 1
+    t = oracle.Trie(wl.patterns)
+    probe = 1 << 18
+    t0 = time.perf_counter()
+    t.scan(wl.text, 0, probe, threads=cores)
+    rate = probe / max(time.perf_counter() - t0, 1e-6)
+    n = int(min(len(wl.text), max(probe, rate * seconds)))
+    t0 = time.perf_counter()
+    t.scan(wl.text, 0, n, threads=cores)
+    dt = time.perf_counter() - t0
+    return {"value": round(8 * n / dt / 1e9, 4), "unit": "Gbps", "cores": cores,
+            "kind": "oracle",
+            "sample": f"start positions 0..{n} of the 256 MiB paper-scale text "
+                      f"({n / len(wl.text) * 100:.2f}%), PFAC pointer-trie walk, "
+                      f"{cores} threads, {dt:.1f} s"}
+
+
+def run_reference(args, rank, world):
+    """CPU oracle arm: rank 0 only; each step a bounded sample."""
+    if rank != 0:
+        return
+    from paper_1702_03657_gb300 import workloads as W
+    import oracle
+    wl = W.paper_scale(0, text_bytes=TEXT_BYTES, n_patterns=N_PATTERNS)
+    cores = os.cpu_count() or 1
+    t = oracle.Trie(wl.patterns)
+    probe = 1 << 18
+    t0 = time.perf_counter()
+    t.scan(wl.text, 0, probe, threads=cores)
+    rate = probe / max(time.perf_counter() - t0, 1e-6)
+    budget = 90.0
+    per_step = int(max(4096, min(len(wl.text) // 2, rate * budget / max(1, args.steps + args.warmup))))
+    rng = np.random.Generator(np.random.MT19937(1))
+    starts = rng.integers(0, len(wl.text) - per_step, size=args.steps + args.warmup)
+    for i in range(args.warmup):
+        t.scan(wl.text, int(starts[i]), int(starts[i]) + per_step, threads=cores)
+    t0 = time.perf_counter()
+    for i in range(args.warmup, args.warmup + args.steps):
+        t.scan(wl.text, int(starts[i]), int(starts[i]) + per_step, threads=cores)
+    dt = time.perf_counter() - t0
+    value = 8 * per_step * args.steps / dt / 1e9
+    sample = (f"{per_step} consecutive start positions per step at seeded random offsets "
+              f"of the 256 MiB paper-scale text; PFAC pointer-trie walk on {cores} threads")
+    line = {"impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": "Gbps",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(dt / args.steps * 1e3, 4), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample_positions_per_step": per_step},
+            "cpu_baseline": {"value": round(value, 4), "unit": "Gbps", "cores": cores,
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": round(value, 4), "unit": "Gbps", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+
+    import torch
+    import torch.distributed as dist
+
+    from paper_1702_03657_gb300 import pm
+    from paper_1702_03657_gb300 import workloads as W
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    pm.load()
+
+    wl = W.paper_scale(rank, text_bytes=TEXT_BYTES, n_patterns=N_PATTERNS)
+    trie = pm.pm_build(wl.patterns)
+    stats = pm.pm_stats(trie)
+    cfg = pm.pm_get_config(trie)
+    n = len(wl.text)
+    text = torch.from_numpy(wl.text).cuda()
+    ids = torch.empty(n, dtype=torch.int32, device="cuda")
+    cnt = torch.empty(1, dtype=torch.int64, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    # trie-lookup count (instrumented kernel, outside the timed region)
+    look = torch.zeros(1, dtype=torch.int64, device="cuda")
+    pm.pm_scan_ex(trie, text, None, ids, cnt, lookups=look)
+    torch.cuda.synchronize()
+    lookups = int(look.item())
+
+    for _ in range(max(args.warmup, 3)):
+        pm.pm_scan(trie, text, ids, cnt)
+    torch.cuda.synchronize()
+
+    K = args.steps
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(K + 1)]
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev[0].record(stream)
+    for i in range(K):
+        pm.pm_scan(trie, text, ids, cnt)
+        ev[i + 1].record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clocks.stop()
+    step_ms = [ev[i].elapsed_time(ev[i + 1]) for i in range(K)]
+    total_ms = ev[0].elapsed_time(ev[K])
+    if world > 1:
+        tt = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        total_ms = float(tt.item())
+    count = int(cnt.item())
+
+    gbps = 8.0 * n * world * K / (total_ms / 1e3) / 1e9
+    avg_launch_s = statistics.mean(step_ms) / 1e3
+    alg_bytes = n + 4 * n + 8                   # text read + int32 ids + count
+    achieved = alg_bytes / avg_launch_s / 1e9   # GB/s
+    peak, peak_kind = measured_peak_hbm()
+    traffic = profiled_traffic()
+
+    # end to end through the C ABI with host buffers (pm_scan_host)
+    h_text = torch.from_numpy(wl.text).pin_memory()
+    h_ids = torch.empty(n, dtype=torch.int32).pin_memory()
+    hn, hi = h_text.numpy(), h_ids.numpy()
+    pm.pm_scan_host(trie, hn, hi)
+    if world > 1:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        hc = pm.pm_scan_host(trie, hn, hi)
+    e2e_s = time.perf_counter() - t0
+    if world > 1:
+        tt = torch.tensor([e2e_s], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e_s = float(tt.item())
+    chunk = 32 << 20
+    nchunks = (n + chunk - 1) // chunk
+    h2d = n + (nchunks - 1) * (stats["max_len"] - 1)
+    d2h = 4 * n + 8 * nchunks
+    e2e = {"value": round(8.0 * n * world * args.e2e_steps / e2e_s / 1e9, 2), "unit": "Gbps",
+           "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+           "api": "pm_scan_host (pinned host text in, host ids + count out)"}
+    assert hc == count, "pm_scan_host count differs from pm_scan"
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        cpu = cpu_baseline(wl, args.cpu_seconds)
+    line = {
+        "metric": METRIC, "value": round(gbps, 2), "unit": "Gbps", "n_gpus": world,
+        "steps": K, "warmup": args.warmup, "ms_per_step": round(total_ms / K, 5),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "text_bytes": n, "patterns": N_PATTERNS,
+                   "launch": cfg, "l2": "inputs larger than L2 (256 MiB text + 1 GiB ids "
+                                        "per step), no flush",
+                   "parallelism": f"text sharded per rank x{world} (independent texts)"},
+        "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
+                     "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": traffic,
+                     "peak_kind": peak_kind,
+                     "algorithmic_bytes_per_launch": alg_bytes,
+                     "trie_term": {"lookups": lookups,
+                                   "lookups_per_byte": round(lookups / n, 4),
+                                   "bytes": 4 * lookups}},
+        "e2e": e2e,
+        "gpu_launches": K,
+        "clocks": clocks.summary(),
+        "cpu_baseline": cpu,
+        "trie": {k: stats[k] for k in ("n_nodes", "nnz", "csr_bytes", "dense256_bytes",
+                                       "bitmap36_bytes", "crs_elements", "alphabet",
+                                       "dense_k_max")},
+        "matches": count,
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

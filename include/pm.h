@@ -1,0 +1,195 @@
+/*
+ * pm.h -- C ABI of libpm: multi-pattern matching by the parallel
+ * failure-less Aho-Corasick (PFAC) scan over a compressed-row-storage trie,
+ * on one GB300 GPU (sm_103a).
+ *
+ * Problem (Section II-B of "Trie Compression for GPU Accelerated
+ * Multi-Pattern Matching"): find the patterns of a set P in a text T.
+ * Method (Section II-C): one walk starts at every byte of T, follows the
+ * pattern trie while the text keeps matching and terminates at the first
+ * mismatch -- no failure links. Trie (Section III): built breadth-first,
+ * stored pointer-free in BFS order and compressed as compressed row storage
+ * (row_ptr, sorted byte column, next state), 2*nnz+n+1 elements.
+ *
+ * Output of a scan, for every start position i of a text:
+ *   ids[i] = id of the longest pattern p with T[i .. i+|p|) == p, else -1;
+ *   count  = number of (start position, distinct pattern) occurrences.
+ * A pattern's id is the index of its first occurrence in the list given to
+ * pm_build; later duplicates are dropped. A walk never crosses the end of
+ * its own text (no padding, no wrap-around).
+ *
+ * Conventions
+ *  - Every function returns PM_OK (0) or a negative PM_ERR_* code and also
+ *    records it for pm_last_error() on the calling thread. No C++ exception
+ *    crosses this boundary.
+ *  - Pointers named d_* are CUDA device pointers on the current device;
+ *    h_* are host pointers. The caller owns every buffer it passes; libpm
+ *    owns only what a pm_trie / pm_server handle holds.
+ *  - pm_stream is the driver stream type (identical to cudaStream_t); NULL
+ *    is the legacy default stream. Scans are asynchronous on that stream.
+ *  - Errors raised inside a kernel (a bounded wait that ran out, a bounds
+ *    violation in the checked scan) are recorded in a device word and
+ *    reported by pm_device_error(); the kernel returns instead of trapping.
+ */
+#ifndef PM_H
+#define PM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- error codes ------------------------------------------------------ */
+#define PM_OK                    0
+#define PM_ERR_INVAL            -1  /* bad argument (null, size, alignment)   */
+#define PM_ERR_NOMEM            -2  /* host or device allocation failed       */
+#define PM_ERR_EMPTY_PATTERN    -3  /* a pattern of length 0                  */
+#define PM_ERR_PATTERN_TOO_LONG -4  /* a pattern longer than PM_MAX_PATTERN_LEN */
+#define PM_ERR_CUDA             -5  /* a CUDA runtime call failed             */
+#define PM_ERR_TIMEOUT          -6  /* a bounded wait ran out                 */
+#define PM_ERR_BOUNDS           -7  /* checked scan saw an out-of-range index */
+#define PM_ERR_BUSY             -8  /* serving: no slot or arena space now    */
+#define PM_ERR_NOT_FOUND        -9  /* serving: unknown request id            */
+#define PM_ERR_HOST_ONLY       -10  /* handle has no device copy              */
+
+#define PM_MAX_PATTERN_LEN 4096u
+
+typedef struct CUstream_st *pm_stream;
+typedef struct pm_trie pm_trie;
+
+/* Result buffers of one scan, both caller-owned DEVICE memory:
+ *   ids   int32[len], one entry per start position;
+ *   count int64[1], overwritten (not accumulated) by the scan. */
+typedef struct {
+    int32_t *ids;
+    int64_t *count;
+} pm_result;
+
+/* Sizes of a built trie (Section III; Section V for the 36-byte node). */
+typedef struct {
+    uint64_t n_patterns;     /* distinct patterns (= final nodes)               */
+    uint64_t n_duplicates;   /* input patterns dropped as repeats               */
+    uint64_t n_nodes;        /* trie nodes including the root (CRS rows n)      */
+    uint64_t nnz;            /* CRS non-zeros = trie edges = n_nodes - 1        */
+    uint32_t min_len;        /* shortest pattern (0 if none)                    */
+    uint32_t max_len;        /* longest pattern = trie depth                    */
+    uint32_t alphabet;       /* byte classes C: bytes used by patterns, +1 for  */
+                             /* "any other byte" unless all 256 are used        */
+    uint32_t dense_k_max;    /* deepest dense prefix table built                */
+    uint64_t crs_elements;   /* 2*nnz + n + 1 (Section III's storage count)     */
+    uint64_t csr_bytes;      /* row_ptr u32[n+1] + col u8[nnz] + next i32[nnz]  */
+                             /* + final_id i32[n]                               */
+    uint64_t dense256_bytes; /* uncompressed 256-wide state table: 256*4*n      */
+    uint64_t bitmap36_bytes; /* 256-bit bitmap + 4-byte offset per node: 36*n   */
+    uint64_t device_bytes;   /* everything the handle holds on the device      */
+} pm_trie_stats;
+
+/* Launch configuration of the scan kernel (picked by an autotuner). */
+typedef struct {
+    int32_t threads;      /* threads per CTA: 128, 256, 512 or 1024           */
+    int32_t tile;         /* text bytes per tile: multiple of 4*threads, <= 64 KiB */
+    int32_t dense_k;      /* trie levels resolved by the dense prefix table,  */
+                          /* 1 .. dense_k_max                                 */
+    int32_t childmask;    /* 1: test a 32-bit child filter of the depth-k     */
+                          /* node before walking its CRS row                  */
+    int32_t row_search;   /* 0: linear, 1: binary search of the byte column   */
+    int32_t ctas_per_sm;  /* persistent grid = SMs * ctas_per_sm (0: maximum) */
+    int32_t stages;       /* text tiles in flight per CTA (TMA), 2..4         */
+    int32_t checked;      /* 1: bounds-checked scan (PM_ERR_BOUNDS on error)  */
+} pm_config;
+
+/* ---- trie construction (Section III, steps I, II, VI and the CRS step) --
+ * Builds the trie of patterns[0..n) (lengths[j] bytes each; any byte value,
+ * NUL included) breadth-first with children in ascending byte order,
+ * compresses it to CRS, derives the dense prefix tables of the top levels,
+ * and copies everything to the current CUDA device. Inputs are copied; the
+ * caller may free them on return. n == 0 is allowed (nothing ever matches).
+ * *footprint_bytes (optional) receives csr_bytes.
+ * Errors: PM_ERR_INVAL (null pointers with n > 0, out == NULL),
+ *         PM_ERR_EMPTY_PATTERN, PM_ERR_PATTERN_TOO_LONG, PM_ERR_NOMEM,
+ *         PM_ERR_CUDA (no device, copy failed). *out is NULL on error. */
+int pm_build(const uint8_t *const *patterns, const uint32_t *lengths, uint32_t n,
+             pm_trie **out, uint64_t *footprint_bytes);
+
+/* As pm_build, but keeps the trie on the host only (no CUDA call is made):
+ * for footprint reports and host-side checks. Scans on such a handle fail
+ * with PM_ERR_HOST_ONLY. */
+int pm_build_host(const uint8_t *const *patterns, const uint32_t *lengths,
+                  uint32_t n, pm_trie **out, uint64_t *footprint_bytes);
+
+/* Frees the handle and its device memory. NULL is ignored. The caller must
+ * ensure no scan on it is still running. */
+void pm_free(pm_trie *h);
+
+/* Sizes of the trie. Errors: PM_ERR_INVAL. */
+int pm_stats(const pm_trie *h, pm_trie_stats *s);
+
+/* Host copies of the CRS arrays (Section III): row_ptr u32[n+1], col
+ * u8[nnz] (ascending within each row), next i32[nnz] (child node), final_id
+ * i32[n] (-1 if no pattern ends at the node). Any output may be NULL.
+ * Sizes come from pm_stats. Errors: PM_ERR_INVAL. */
+int pm_export_csr(const pm_trie *h, uint32_t *row_ptr, uint8_t *col,
+                  int32_t *next, int32_t *final_id);
+
+/* The handle's current launch configuration / replace it after validation.
+ * pm_set_config must not run concurrently with scans on the handle.
+ * Errors: PM_ERR_INVAL (a field out of range). */
+int pm_get_config(const pm_trie *h, pm_config *cfg);
+int pm_set_config(pm_trie *h, const pm_config *cfg);
+
+/* ---- scans (Section II-C) ----------------------------------------------
+ * pm_scan: one text d_text[0..len) (device memory, any alignment). Writes
+ * out.ids[0..len) and *out.count, asynchronously on `stream`. len == 0 is
+ * legal (count 0). The handle is read-only during scans, so concurrent scans
+ * on different streams are safe; out.ids must not alias the text.
+ * Errors: PM_ERR_INVAL (null pointers with len > 0), PM_ERR_HOST_ONLY,
+ *         PM_ERR_CUDA (launch failed). */
+int pm_scan(const pm_trie *h, const uint8_t *d_text, uint64_t len,
+            pm_result out, pm_stream stream);
+
+/* pm_scan_batch: ntexts texts stored back to back in d_texts; text t is
+ * d_texts[d_offsets[t] .. d_offsets[t+1]) with d_offsets a DEVICE array of
+ * ntexts+1 non-decreasing u64 starting at 0. Writes d_ids[0 .. total)
+ * (same offsets as the texts) and d_counts[0..ntexts) (overwritten). One
+ * persistent launch, no host synchronisation; can be captured in a CUDA
+ * graph. Matches never cross a text boundary.
+ * Errors: PM_ERR_INVAL, PM_ERR_HOST_ONLY, PM_ERR_CUDA. */
+int pm_scan_batch(const pm_trie *h, const uint8_t *d_texts,
+                  const uint64_t *d_offsets, uint32_t ntexts,
+                  int32_t *d_ids, int64_t *d_counts, pm_stream stream);
+
+/* As pm_scan_batch with an explicit configuration (NULL: the handle's) and
+ * an optional DEVICE u64 d_lookups that receives the number of trie
+ * transitions attempted (slower instrumented kernel; for the roofline's
+ * trie term). With d_offsets == NULL the input is one text of `len` bytes
+ * and d_counts has one entry; otherwise `len` is ignored. */
+int pm_scan_ex(const pm_trie *h, const uint8_t *d_texts,
+               const uint64_t *d_offsets, uint32_t ntexts, uint64_t len,
+               int32_t *d_ids, int64_t *d_counts, uint64_t *d_lookups,
+               const pm_config *cfg, pm_stream stream);
+
+/* ---- host buffers ---------------------------------------------------------
+ * pm_scan_host: scans a HOST text h_text[0..len) and returns the results in
+ * host memory (h_ids int32[len], *h_count). The text is cut into chunks
+ * that overlap by max_len-1 bytes (Section II-B's overlap rule); copies in,
+ * scans and copies out are pipelined over two internal streams using device
+ * buffers owned by the handle. Pinned host memory gives full copy speed.
+ * Blocks until the results are on the host. Not reentrant per handle.
+ * Errors: PM_ERR_INVAL, PM_ERR_HOST_ONLY, PM_ERR_NOMEM, PM_ERR_CUDA. */
+int pm_scan_host(pm_trie *h, const uint8_t *h_text, uint64_t len,
+                 int32_t *h_ids, int64_t *h_count);
+
+/* ---- errors ------------------------------------------------------------ */
+/* Reads and clears the device-side error word (synchronises the device):
+ * *code = PM_OK, PM_ERR_TIMEOUT or PM_ERR_BOUNDS. Errors: PM_ERR_CUDA. */
+int pm_device_error(int *code);
+const char *pm_strerror(int code);   /* static string, never NULL          */
+int pm_last_error(void);             /* last code returned on this thread  */
+const char *pm_last_error_msg(void); /* detail for it, thread-local string */
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PM_H */

@@ -1,0 +1,482 @@
+// C ABI of libpm (include/pm.h): handle management, device upload, argument
+// checks and error reporting around the host builder and the scan kernels.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "pm_internal.h"
+
+namespace {
+
+thread_local int t_last = PM_OK;
+thread_local std::string t_msg;
+
+int fail(int code, const std::string &msg)
+{
+    t_last = code;
+    t_msg = msg;
+    return code;
+}
+
+int ok()
+{
+    t_last = PM_OK;
+    t_msg.clear();
+    return PM_OK;
+}
+
+int cuda_fail(const char *what, cudaError_t e)
+{
+    return fail(PM_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+uint64_t align256(uint64_t x) { return (x + 255) & ~255ull; }
+
+uint64_t csr_bytes(const pm::HostTrie &h)
+{
+    uint64_t n = h.final_id.size(), nnz = h.col.size();
+    return 4 * (n + 1) + nnz + 4 * nnz + 4 * n;
+}
+
+// Shared memory a CTA may use on this device (opt-in limit).
+int max_smem_optin(int device)
+{
+    int v = 0;
+    if (device < 0 || cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, device) !=
+                          cudaSuccess)
+        v = 227 * 1024;
+    return v;
+}
+
+// Default launch configuration: the deepest dense table, the child filter
+// when it exists, three tiles in flight; shrunk until it fits the SM.
+pm_config default_config(const pm_trie *h, int smem_limit)
+{
+    pm_config c{};
+    c.threads = 512;
+    c.tile = 16384;
+    c.dense_k = (int32_t)h->host.dense_k_max;
+    c.childmask = h->host.childmask[c.dense_k].empty() ? 0 : 1;
+    c.row_search = 0;
+    c.ctas_per_sm = 0;
+    c.stages = 3;
+    c.checked = 0;
+    // static shared memory of the kernel (reduction scratch) + slack
+    const uint64_t limit = (uint64_t)smem_limit - 1024;
+    while (pm::scan_smem_bytes(h->dev, c) > limit) {
+        if (c.stages > 2) c.stages = 2;
+        else if (c.tile > 4 * c.threads) c.tile /= 2;
+        else if (c.childmask) c.childmask = 0;
+        else if (c.dense_k > 1) {
+            --c.dense_k;
+            c.childmask = h->host.childmask[c.dense_k].empty() ? 0 : 1;
+            c.tile = 16384;
+        } else break;
+    }
+    return c;
+}
+
+int validate_config(const pm_trie *h, const pm_config &c, std::string &why)
+{
+    if (c.threads != 128 && c.threads != 256 && c.threads != 512) {
+        why = "threads must be 128, 256 or 512";
+        return PM_ERR_INVAL;
+    }
+    if (c.tile < 4 * c.threads || c.tile > 65536 || c.tile % (4 * c.threads) != 0) {
+        why = "tile must be a multiple of 4*threads in [4*threads, 65536]";
+        return PM_ERR_INVAL;
+    }
+    if (c.dense_k < 1 || (uint32_t)c.dense_k > h->host.dense_k_max) {
+        why = "dense_k must be in 1..dense_k_max";
+        return PM_ERR_INVAL;
+    }
+    if (c.childmask && h->host.childmask[c.dense_k].empty()) {
+        why = "no child filter table at this dense_k";
+        return PM_ERR_INVAL;
+    }
+    if (c.stages < 2 || c.stages > 4) {
+        why = "stages must be 2..4";
+        return PM_ERR_INVAL;
+    }
+    if (c.ctas_per_sm < 0 || c.ctas_per_sm > 32) {
+        why = "ctas_per_sm must be 0..32";
+        return PM_ERR_INVAL;
+    }
+    if (c.row_search < 0 || c.row_search > 1 || c.checked < 0 || c.checked > 1 ||
+        c.childmask < 0 || c.childmask > 1) {
+        why = "row_search, childmask and checked are 0 or 1";
+        return PM_ERR_INVAL;
+    }
+    uint64_t need = pm::scan_smem_bytes(h->dev, c);
+    if (need + 1024 > (uint64_t)max_smem_optin(h->device)) {
+        why = "configuration needs " + std::to_string(need) + " bytes of shared memory";
+        return PM_ERR_INVAL;
+    }
+    return PM_OK;
+}
+
+// Host-side view for TrieDev fields that do not depend on the device.
+void fill_dev_sizes(pm_trie *h)
+{
+    pm::TrieDev &d = h->dev;
+    const pm::HostTrie &t = h->host;
+    d.C = t.C;
+    d.n_nodes = (uint32_t)t.final_id.size();
+    d.nnz = (uint32_t)t.col.size();
+    d.min_len = t.n_patterns ? t.min_len : 0xFFFFFFFFu;
+    d.max_len = t.max_len;
+    d.dense_k_max = t.dense_k_max;
+    for (int k = 0; k <= pm::kMaxDenseK; ++k) {
+        d.dense_words[k] = (uint32_t)(t.dense[k].size() / 2);
+        d.first[k] = t.first[k];
+        d.nlevel[k] = t.nlevel[k];
+    }
+}
+
+int upload(pm_trie *h)
+{
+    const pm::HostTrie &t = h->host;
+    const uint64_t n = t.final_id.size(), nnz = t.col.size();
+    struct Part {
+        const void *src;
+        uint64_t bytes;
+        uint64_t off;
+    };
+    std::vector<int2> emit(n);
+    for (uint64_t v = 0; v < n; ++v) emit[v] = make_int2(t.best[v], t.nfinal[v]);
+    std::vector<Part> parts;
+    uint64_t off = 0;
+    auto add = [&](const void *src, uint64_t bytes) {
+        parts.push_back({src, bytes, off});
+        off = align256(off + std::max<uint64_t>(bytes, 16));
+        return parts.size() - 1;
+    };
+    size_t i_row = add(t.row_ptr.data(), 4 * (n + 1));
+    size_t i_col = add(t.col.data(), nnz);
+    size_t i_next = add(t.next.data(), 4 * nnz);
+    size_t i_emit = add(emit.data(), 8 * n);
+    size_t i_cls = add(t.cls, 256);
+    size_t i_dense[pm::kMaxDenseK + 1] = {};
+    size_t i_cm[pm::kMaxDenseK + 1] = {};
+    for (int k = 1; k <= pm::kMaxDenseK; ++k) {
+        i_dense[k] = t.dense[k].empty() ? (size_t)-1 : add(t.dense[k].data(), 4 * t.dense[k].size());
+        i_cm[k] = t.childmask[k].empty() ? (size_t)-1
+                                         : add(t.childmask[k].data(), 4 * t.childmask[k].size());
+    }
+    cudaError_t e = cudaGetDevice(&h->device);
+    if (e != cudaSuccess) return cuda_fail("cudaGetDevice", e);
+    e = cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, h->device);
+    if (e != cudaSuccess) return cuda_fail("cudaDeviceGetAttribute", e);
+    void *arena = nullptr;
+    e = cudaMalloc(&arena, off);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(PM_ERR_NOMEM, "cudaMalloc of " + std::to_string(off) + " bytes failed");
+    }
+    h->d_arena = arena;
+    h->device_bytes = off;
+    uint8_t *base = static_cast<uint8_t *>(arena);
+    for (const Part &p : parts) {
+        if (!p.bytes) continue;
+        e = cudaMemcpy(base + p.off, p.src, p.bytes, cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return cuda_fail("cudaMemcpy", e);
+    }
+    pm::TrieDev &d = h->dev;
+    d.row_ptr = reinterpret_cast<const uint32_t *>(base + parts[i_row].off);
+    d.col = base + parts[i_col].off;
+    d.next = reinterpret_cast<const int32_t *>(base + parts[i_next].off);
+    d.emit = reinterpret_cast<const int2 *>(base + parts[i_emit].off);
+    d.cls = base + parts[i_cls].off;
+    for (int k = 1; k <= pm::kMaxDenseK; ++k) {
+        d.dense[k] = i_dense[k] == (size_t)-1 ? nullptr
+                                              : reinterpret_cast<const uint2 *>(base + parts[i_dense[k]].off);
+        d.childmask[k] = i_cm[k] == (size_t)-1
+                             ? nullptr
+                             : reinterpret_cast<const uint32_t *>(base + parts[i_cm[k]].off);
+    }
+    return PM_OK;
+}
+
+int build_common(const uint8_t *const *patterns, const uint32_t *lengths, uint32_t n,
+                 pm_trie **out, uint64_t *footprint, bool device)
+{
+    if (!out) return fail(PM_ERR_INVAL, "out is NULL");
+    *out = nullptr;
+    pm_trie *h = new (std::nothrow) pm_trie();
+    if (!h) return fail(PM_ERR_NOMEM, "handle allocation failed");
+    std::string msg;
+    int rc;
+    try {
+        rc = pm::build_host_trie(patterns, lengths, n, h->host, msg);
+    } catch (const std::bad_alloc &) {
+        rc = PM_ERR_NOMEM;
+        msg = "host allocation failed while building the trie";
+    }
+    if (rc != PM_OK) {
+        delete h;
+        return fail(rc, msg);
+    }
+    fill_dev_sizes(h);
+    if (device) {
+        rc = upload(h);
+        if (rc != PM_OK) {
+            std::string keep = t_msg;
+            pm_free(h);
+            return fail(rc, keep);
+        }
+    }
+    h->cfg = default_config(h, max_smem_optin(h->device));
+    if (footprint) *footprint = csr_bytes(h->host);
+    *out = h;
+    return ok();
+}
+
+int scan_common(const pm_trie *h, const uint8_t *d_texts, const uint64_t *d_offsets,
+                uint32_t ntexts, uint64_t len, uint64_t limit, int32_t *d_ids, int64_t *d_counts,
+                uint64_t *d_lookups, const pm_config *cfg, pm_stream stream)
+{
+    if (!h) return fail(PM_ERR_INVAL, "handle is NULL");
+    if (!h->d_arena) return fail(PM_ERR_HOST_ONLY, "handle was built with pm_build_host");
+    const bool batch = d_offsets != nullptr;
+    if (!d_counts) return fail(PM_ERR_INVAL, "counts is NULL");
+    if (batch ? ntexts > 0 && (!d_texts || !d_ids) : len > 0 && (!d_texts || !d_ids))
+        return fail(PM_ERR_INVAL, "text or ids is NULL");
+    pm_config c = cfg ? *cfg : h->cfg;
+    if (cfg) {
+        std::string why;
+        if (validate_config(h, c, why) != PM_OK) return fail(PM_ERR_INVAL, why);
+    }
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail("cudaGetDevice", e);
+    if (dev != h->device)
+        return fail(PM_ERR_INVAL, "current device differs from the device the trie was built on");
+    pm::ScanArgs a{};
+    a.text = d_texts;
+    a.offsets = d_offsets;
+    a.ntexts = batch ? ntexts : 1;
+    a.len = len;
+    a.limit = limit;
+    a.ids = d_ids;
+    a.counts = d_counts;
+    a.lookups = reinterpret_cast<unsigned long long *>(d_lookups);
+    std::string msg;
+    int rc = pm::launch_scan(h->dev, c, a, stream, h->sms, msg);
+    if (rc != PM_OK) return fail(rc, msg);
+    return ok();
+}
+
+}  // namespace
+
+extern "C" {
+
+int pm_build(const uint8_t *const *patterns, const uint32_t *lengths, uint32_t n, pm_trie **out,
+             uint64_t *footprint_bytes)
+{
+    return build_common(patterns, lengths, n, out, footprint_bytes, true);
+}
+
+int pm_build_host(const uint8_t *const *patterns, const uint32_t *lengths, uint32_t n,
+                  pm_trie **out, uint64_t *footprint_bytes)
+{
+    return build_common(patterns, lengths, n, out, footprint_bytes, false);
+}
+
+void pm_free(pm_trie *h)
+{
+    if (!h) return;
+    for (void *&s : h->h_streams)
+        if (s) {
+            cudaStreamDestroy(reinterpret_cast<cudaStream_t>(s));
+            s = nullptr;
+        }
+    if (h->d_hbuf_text) cudaFree(h->d_hbuf_text);
+    if (h->d_hbuf_ids) cudaFree(h->d_hbuf_ids);
+    if (h->d_hbuf_counts) cudaFree(h->d_hbuf_counts);
+    if (h->h_hbuf_counts) cudaFreeHost(h->h_hbuf_counts);
+    if (h->d_arena) cudaFree(h->d_arena);
+    delete h;
+}
+
+int pm_stats(const pm_trie *h, pm_trie_stats *s)
+{
+    if (!h || !s) return fail(PM_ERR_INVAL, "handle or stats is NULL");
+    const pm::HostTrie &t = h->host;
+    std::memset(s, 0, sizeof(*s));
+    const uint64_t n = t.final_id.size(), nnz = t.col.size();
+    s->n_patterns = t.n_patterns;
+    s->n_duplicates = t.n_duplicates;
+    s->n_nodes = n;
+    s->nnz = nnz;
+    s->min_len = t.min_len;
+    s->max_len = t.max_len;
+    s->alphabet = t.C;
+    s->dense_k_max = t.dense_k_max;
+    s->crs_elements = 2 * nnz + n + 1;
+    s->csr_bytes = csr_bytes(t);
+    s->dense256_bytes = 256ull * 4 * n;
+    s->bitmap36_bytes = 36ull * n;
+    s->device_bytes = h->device_bytes;
+    return ok();
+}
+
+int pm_export_csr(const pm_trie *h, uint32_t *row_ptr, uint8_t *col, int32_t *next,
+                  int32_t *final_id)
+{
+    if (!h) return fail(PM_ERR_INVAL, "handle is NULL");
+    const pm::HostTrie &t = h->host;
+    if (row_ptr) std::memcpy(row_ptr, t.row_ptr.data(), 4 * t.row_ptr.size());
+    if (col && !t.col.empty()) std::memcpy(col, t.col.data(), t.col.size());
+    if (next && !t.next.empty()) std::memcpy(next, t.next.data(), 4 * t.next.size());
+    if (final_id) std::memcpy(final_id, t.final_id.data(), 4 * t.final_id.size());
+    return ok();
+}
+
+int pm_get_config(const pm_trie *h, pm_config *cfg)
+{
+    if (!h || !cfg) return fail(PM_ERR_INVAL, "handle or config is NULL");
+    *cfg = h->cfg;
+    return ok();
+}
+
+int pm_set_config(pm_trie *h, const pm_config *cfg)
+{
+    if (!h || !cfg) return fail(PM_ERR_INVAL, "handle or config is NULL");
+    std::string why;
+    if (validate_config(h, *cfg, why) != PM_OK) return fail(PM_ERR_INVAL, why);
+    h->cfg = *cfg;
+    return ok();
+}
+
+int pm_scan(const pm_trie *h, const uint8_t *d_text, uint64_t len, pm_result out, pm_stream stream)
+{
+    return scan_common(h, d_text, nullptr, 1, len, len, out.ids, out.count, nullptr, nullptr,
+                       stream);
+}
+
+int pm_scan_batch(const pm_trie *h, const uint8_t *d_texts, const uint64_t *d_offsets,
+                  uint32_t ntexts, int32_t *d_ids, int64_t *d_counts, pm_stream stream)
+{
+    if (!d_offsets) return fail(PM_ERR_INVAL, "offsets is NULL");
+    return scan_common(h, d_texts, d_offsets, ntexts, 0, 0, d_ids, d_counts, nullptr, nullptr,
+                       stream);
+}
+
+int pm_scan_ex(const pm_trie *h, const uint8_t *d_texts, const uint64_t *d_offsets,
+               uint32_t ntexts, uint64_t len, int32_t *d_ids, int64_t *d_counts,
+               uint64_t *d_lookups, const pm_config *cfg, pm_stream stream)
+{
+    return scan_common(h, d_texts, d_offsets, ntexts, len, len, d_ids, d_counts, d_lookups, cfg,
+                       stream);
+}
+
+int pm_scan_host(pm_trie *h, const uint8_t *h_text, uint64_t len, int32_t *h_ids,
+                 int64_t *h_count)
+{
+    if (!h) return fail(PM_ERR_INVAL, "handle is NULL");
+    if (!h->d_arena) return fail(PM_ERR_HOST_ONLY, "handle was built with pm_build_host");
+    if (!h_count || (len > 0 && (!h_text || !h_ids)))
+        return fail(PM_ERR_INVAL, "text, ids or count is NULL");
+    *h_count = 0;
+    if (len == 0) return ok();
+    // Chunks of CH start positions; each chunk also copies the next
+    // overlap = max_len - 1 bytes so that its last walks can finish.
+    const uint64_t CH = 32ull << 20;
+    const uint64_t overlap = h->host.max_len ? h->host.max_len - 1 : 0;
+    const uint64_t slot = (CH + overlap + 255) & ~255ull;
+    cudaError_t e;
+    if (!h->h_streams[0]) {
+        for (void *&s : h->h_streams) {
+            cudaStream_t st;
+            e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+            if (e != cudaSuccess) return cuda_fail("cudaStreamCreate", e);
+            s = st;
+        }
+    }
+    if (h->hbuf_chunk != slot) {
+        if (h->d_hbuf_text) cudaFree(h->d_hbuf_text);
+        if (h->d_hbuf_ids) cudaFree(h->d_hbuf_ids);
+        if (h->d_hbuf_counts) cudaFree(h->d_hbuf_counts);
+        if (h->h_hbuf_counts) cudaFreeHost(h->h_hbuf_counts);
+        h->d_hbuf_text = nullptr;
+        h->d_hbuf_ids = nullptr;
+        h->d_hbuf_counts = nullptr;
+        h->h_hbuf_counts = nullptr;
+        h->hbuf_chunk = 0;
+        if (cudaMalloc(&h->d_hbuf_text, 2 * slot) != cudaSuccess ||
+            cudaMalloc(&h->d_hbuf_ids, 2 * 4 * CH) != cudaSuccess ||
+            cudaMalloc(&h->d_hbuf_counts, 2 * 8) != cudaSuccess ||
+            cudaMallocHost(&h->h_hbuf_counts, 8 * 4096) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(PM_ERR_NOMEM, "pm_scan_host staging buffers");
+        }
+        h->hbuf_chunk = slot;
+    }
+    const uint64_t nchunks = (len + CH - 1) / CH;
+    int64_t total = 0;
+    for (uint64_t c0 = 0; c0 < nchunks; c0 += 4096) {
+        const uint64_t c1 = std::min(nchunks, c0 + 4096);
+        for (uint64_t c = c0; c < c1; ++c) {
+            const int b = (int)(c & 1);
+            cudaStream_t st = reinterpret_cast<cudaStream_t>(h->h_streams[b]);
+            const uint64_t s = c * CH;
+            const uint64_t npos = std::min(CH, len - s);
+            const uint64_t nread = std::min(npos + overlap, len - s);
+            uint8_t *dt = h->d_hbuf_text + b * slot;
+            int32_t *di = h->d_hbuf_ids + b * CH;
+            int64_t *dc = h->d_hbuf_counts + b;
+            e = cudaMemcpyAsync(dt, h_text + s, nread, cudaMemcpyHostToDevice, st);
+            if (e != cudaSuccess) return cuda_fail("cudaMemcpyAsync H2D", e);
+            int rc = scan_common(h, dt, nullptr, 1, npos, nread, di, dc, nullptr, nullptr,
+                                 reinterpret_cast<pm_stream>(st));
+            if (rc != PM_OK) return rc;
+            e = cudaMemcpyAsync(h_ids + s, di, 4 * npos, cudaMemcpyDeviceToHost, st);
+            if (e != cudaSuccess) return cuda_fail("cudaMemcpyAsync D2H", e);
+            e = cudaMemcpyAsync(h->h_hbuf_counts + (c - c0), dc, 8, cudaMemcpyDeviceToHost, st);
+            if (e != cudaSuccess) return cuda_fail("cudaMemcpyAsync D2H", e);
+        }
+        for (void *s : h->h_streams) {
+            e = cudaStreamSynchronize(reinterpret_cast<cudaStream_t>(s));
+            if (e != cudaSuccess) return cuda_fail("cudaStreamSynchronize", e);
+        }
+        for (uint64_t c = c0; c < c1; ++c) total += h->h_hbuf_counts[c - c0];
+    }
+    *h_count = total;
+    return ok();
+}
+
+int pm_device_error(int *code)
+{
+    if (!code) return fail(PM_ERR_INVAL, "code is NULL");
+    std::string msg;
+    int rc = pm::read_device_error(code, msg);
+    if (rc != PM_OK) return fail(rc, msg);
+    return ok();
+}
+
+const char *pm_strerror(int code)
+{
+    switch (code) {
+    case PM_OK: return "success";
+    case PM_ERR_INVAL: return "invalid argument";
+    case PM_ERR_NOMEM: return "out of memory";
+    case PM_ERR_EMPTY_PATTERN: return "empty pattern";
+    case PM_ERR_PATTERN_TOO_LONG: return "pattern longer than PM_MAX_PATTERN_LEN";
+    case PM_ERR_CUDA: return "CUDA error";
+    case PM_ERR_TIMEOUT: return "bounded wait timed out";
+    case PM_ERR_BOUNDS: return "index out of bounds (checked scan)";
+    case PM_ERR_BUSY: return "no slot or arena space available";
+    case PM_ERR_NOT_FOUND: return "unknown request";
+    case PM_ERR_HOST_ONLY: return "handle has no device copy";
+    default: return "unknown error";
+    }
+}
+
+int pm_last_error(void) { return t_last; }
+
+const char *pm_last_error_msg(void) { return t_msg.c_str(); }
+
+}  // extern "C"

@@ -1,0 +1,291 @@
+"""Thin ctypes binding of libpm (include/pm.h), same names as the C ABI.
+
+Argument marshalling only: torch tensors give device pointers and streams;
+every step of a scan runs in libpm's CUDA kernels. There is no CPU fallback:
+if libpm.so is missing or a call fails, a ``PMError`` is raised.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+from . import build as _build
+
+PM_OK = 0
+PM_ERR_INVAL = -1
+PM_ERR_NOMEM = -2
+PM_ERR_EMPTY_PATTERN = -3
+PM_ERR_PATTERN_TOO_LONG = -4
+PM_ERR_CUDA = -5
+PM_ERR_TIMEOUT = -6
+PM_ERR_BOUNDS = -7
+PM_ERR_BUSY = -8
+PM_ERR_NOT_FOUND = -9
+PM_ERR_HOST_ONLY = -10
+PM_MAX_PATTERN_LEN = 4096
+
+# every symbol include/pm.h declares (checked by the tests)
+EXPORTS = (
+    "pm_build", "pm_build_host", "pm_free", "pm_stats", "pm_export_csr",
+    "pm_get_config", "pm_set_config", "pm_scan", "pm_scan_batch", "pm_scan_ex",
+    "pm_scan_host", "pm_device_error", "pm_strerror", "pm_last_error",
+    "pm_last_error_msg",
+)
+
+
+class PMError(RuntimeError):
+    def __init__(self, code: int, where: str, msg: str = ""):
+        self.code = code
+        super().__init__(f"{where}: {code} ({msg})")
+
+
+class pm_result(C.Structure):
+    _fields_ = [("ids", C.c_void_p), ("count", C.c_void_p)]
+
+
+class pm_trie_stats(C.Structure):
+    _fields_ = [
+        ("n_patterns", C.c_uint64), ("n_duplicates", C.c_uint64),
+        ("n_nodes", C.c_uint64), ("nnz", C.c_uint64),
+        ("min_len", C.c_uint32), ("max_len", C.c_uint32),
+        ("alphabet", C.c_uint32), ("dense_k_max", C.c_uint32),
+        ("crs_elements", C.c_uint64), ("csr_bytes", C.c_uint64),
+        ("dense256_bytes", C.c_uint64), ("bitmap36_bytes", C.c_uint64),
+        ("device_bytes", C.c_uint64),
+    ]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class pm_config(C.Structure):
+    _fields_ = [(f, C.c_int32) for f in (
+        "threads", "tile", "dense_k", "childmask", "row_search",
+        "ctas_per_sm", "stages", "checked")]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+    @staticmethod
+    def from_dict(d):
+        c = pm_config()
+        for f, _ in pm_config._fields_:
+            setattr(c, f, int(d[f]))
+        return c
+
+
+_lib = None
+
+
+def load(path: Optional[str] = None):
+    """Load libpm.so (built in-tree by ``build.build()``)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or _build.LIB
+    if not os.path.exists(path):
+        raise PMError(PM_ERR_CUDA, "load", f"{path} missing: run __graft_entry__.build()")
+    lib = C.CDLL(path)
+    P, u32, u64, i32 = C.c_void_p, C.c_uint32, C.c_uint64, C.c_int32
+    sig = {
+        "pm_build": ([P, P, u32, P, P], C.c_int),
+        "pm_build_host": ([P, P, u32, P, P], C.c_int),
+        "pm_free": ([P], None),
+        "pm_stats": ([P, P], C.c_int),
+        "pm_export_csr": ([P, P, P, P, P], C.c_int),
+        "pm_get_config": ([P, P], C.c_int),
+        "pm_set_config": ([P, P], C.c_int),
+        "pm_scan": ([P, P, u64, pm_result, P], C.c_int),
+        "pm_scan_batch": ([P, P, P, u32, P, P, P], C.c_int),
+        "pm_scan_ex": ([P, P, P, u32, u64, P, P, P, P, P], C.c_int),
+        "pm_scan_host": ([P, P, u64, P, P], C.c_int),
+        "pm_device_error": ([P], C.c_int),
+        "pm_strerror": ([C.c_int], C.c_char_p),
+        "pm_last_error": ([], C.c_int),
+        "pm_last_error_msg": ([], C.c_char_p),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = res
+    _lib = lib
+    return lib
+
+
+def _check(rc: int, where: str):
+    if rc != PM_OK:
+        msg = _lib.pm_last_error_msg().decode(errors="replace")
+        raise PMError(rc, where, msg or _lib.pm_strerror(rc).decode())
+
+
+def _pattern_arrays(patterns):
+    """(keepalive, ptr array, lengths) for a PatternSet or a list of bytes."""
+    if hasattr(patterns, "data") and hasattr(patterns, "off"):
+        data = np.ascontiguousarray(patterns.data, dtype=np.uint8)
+        off = np.asarray(patterns.off, dtype=np.int64)
+    else:
+        pats = [bytes(p) for p in patterns]
+        off = np.zeros(len(pats) + 1, dtype=np.int64)
+        np.cumsum([len(p) for p in pats], out=off[1:])
+        data = np.frombuffer(b"".join(pats) + b"\0", dtype=np.uint8).copy()
+    n = len(off) - 1
+    if data.size == 0:
+        data = np.zeros(1, np.uint8)
+    base = data.ctypes.data
+    ptrs = (C.c_void_p * max(n, 1))(*[base + int(o) for o in off[:-1]])
+    lens = np.ascontiguousarray(np.diff(off), dtype=np.uint32)
+    return (data, ptrs, lens), ptrs, lens, n
+
+
+class Trie:
+    """Owns a pm_trie handle; freed with pm_free."""
+
+    def __init__(self, handle, footprint):
+        self.handle = handle
+        self.footprint = footprint
+
+    def __del__(self):
+        h, self.handle = getattr(self, "handle", None), None
+        if h and _lib is not None:
+            _lib.pm_free(h)
+
+    @property
+    def _as_parameter_(self):
+        return self.handle
+
+
+def pm_build(patterns, host_only: bool = False) -> Trie:
+    lib = load()
+    keep, ptrs, lens, n = _pattern_arrays(patterns)
+    h = C.c_void_p()
+    fp = C.c_uint64()
+    fn = lib.pm_build_host if host_only else lib.pm_build
+    _check(fn(ptrs, lens.ctypes.data if n else None, n, C.byref(h), C.byref(fp)),
+           "pm_build_host" if host_only else "pm_build")
+    return Trie(h.value, fp.value)
+
+
+def pm_build_host(patterns) -> Trie:
+    return pm_build(patterns, host_only=True)
+
+
+def pm_free(trie: Trie):
+    h, trie.handle = trie.handle, None
+    if h:
+        load().pm_free(h)
+
+
+def pm_stats(trie: Trie) -> dict:
+    s = pm_trie_stats()
+    _check(load().pm_stats(trie.handle, C.byref(s)), "pm_stats")
+    return s.as_dict()
+
+
+def pm_export_csr(trie: Trie):
+    st = pm_stats(trie)
+    n, nnz = st["n_nodes"], st["nnz"]
+    row_ptr = np.empty(n + 1, np.uint32)
+    col = np.empty(max(nnz, 1), np.uint8)
+    nxt = np.empty(max(nnz, 1), np.int32)
+    fin = np.empty(n, np.int32)
+    _check(load().pm_export_csr(trie.handle, row_ptr.ctypes.data, col.ctypes.data,
+                                nxt.ctypes.data, fin.ctypes.data), "pm_export_csr")
+    return row_ptr, col[:nnz], nxt[:nnz], fin
+
+
+def pm_get_config(trie: Trie) -> dict:
+    c = pm_config()
+    _check(load().pm_get_config(trie.handle, C.byref(c)), "pm_get_config")
+    return c.as_dict()
+
+
+def pm_set_config(trie: Trie, cfg: dict):
+    c = pm_config.from_dict(cfg)
+    _check(load().pm_set_config(trie.handle, C.byref(c)), "pm_set_config")
+
+
+def _stream_ptr(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(stream.cuda_stream)
+
+
+def _dptr(t, dtype=None, name="tensor"):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise PMError(PM_ERR_INVAL, name, "must be a CUDA tensor")
+    if not t.is_contiguous():
+        raise PMError(PM_ERR_INVAL, name, "must be contiguous")
+    if dtype is not None and t.dtype != dtype:
+        raise PMError(PM_ERR_INVAL, name, f"dtype {t.dtype}, expected {dtype}")
+    return t.data_ptr() if t.numel() else None
+
+
+def _offsets_ptr(offsets):
+    if offsets.element_size() != 8:
+        raise PMError(PM_ERR_INVAL, "offsets", "must be 64-bit (int64 or uint64)")
+    return _dptr(offsets, None, "offsets")
+
+
+def pm_scan(trie: Trie, text, ids, count, stream=None, length: Optional[int] = None):
+    """Scan one device text (uint8 tensor) into ids (int32[len]) and count
+    (int64[1]) on `stream` (default: torch's current stream)."""
+    import torch
+    n = text.numel() if length is None else length
+    out = pm_result(_dptr(ids, torch.int32, "ids"), _dptr(count, torch.int64, "count"))
+    _check(load().pm_scan(trie.handle, _dptr(text, torch.uint8, "text"), n, out,
+                          _stream_ptr(stream)), "pm_scan")
+
+
+def pm_scan_batch(trie: Trie, texts, offsets, ids, counts, stream=None):
+    import torch
+    ntexts = offsets.numel() - 1
+    _check(load().pm_scan_batch(
+        trie.handle, _dptr(texts, torch.uint8, "texts"),
+        _offsets_ptr(offsets),
+        ntexts, _dptr(ids, torch.int32, "ids"), _dptr(counts, torch.int64, "counts"),
+        _stream_ptr(stream)), "pm_scan_batch")
+
+
+def pm_scan_ex(trie: Trie, texts, offsets, ids, counts, lookups=None,
+               cfg: Optional[dict] = None, stream=None, length: Optional[int] = None):
+    import torch
+    ntexts = offsets.numel() - 1 if offsets is not None else 1
+    n = texts.numel() if length is None else length
+    c = pm_config.from_dict(cfg) if cfg is not None else None
+    _check(load().pm_scan_ex(
+        trie.handle, _dptr(texts, torch.uint8, "texts"),
+        _offsets_ptr(offsets) if offsets is not None else None,
+        ntexts, n, _dptr(ids, torch.int32, "ids"), _dptr(counts, torch.int64, "counts"),
+        _dptr(lookups, None, "lookups") if lookups is not None else None,
+        C.byref(c) if c is not None else None, _stream_ptr(stream)), "pm_scan_ex")
+
+
+def pm_scan_host(trie: Trie, text: np.ndarray, ids: np.ndarray) -> int:
+    """Scan a host text (uint8 numpy, ideally pinned) into host ids (int32);
+    returns the count."""
+    assert text.dtype == np.uint8 and ids.dtype == np.int32 and ids.size >= text.size
+    cnt = C.c_int64()
+    _check(load().pm_scan_host(trie.handle, text.ctypes.data if text.size else None,
+                               text.size, ids.ctypes.data if ids.size else None,
+                               C.byref(cnt)), "pm_scan_host")
+    return cnt.value
+
+
+def pm_device_error() -> int:
+    code = C.c_int()
+    _check(load().pm_device_error(C.byref(code)), "pm_device_error")
+    return code.value
+
+
+def pm_strerror(code: int) -> str:
+    return load().pm_strerror(code).decode()
+
+
+def pm_last_error() -> int:
+    return load().pm_last_error()

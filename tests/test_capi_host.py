@@ -1,0 +1,135 @@
+"""The C ABI without a GPU: library load, exported symbols, host-side trie
+construction and CRS compression checked against the oracle and the paper's
+storage formulas (Section III, Section V)."""
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1702_03657_gb300 import build as B
+from paper_1702_03657_gb300 import pm
+from paper_1702_03657_gb300 import workloads as W
+
+
+@pytest.fixture(scope="module")
+def lib():
+    B.build()
+    return pm.load()
+
+
+def header_symbols():
+    src = open(B.INCLUDE + "/pm.h").read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(pm_[a-z_]+)\s*\(", src)))
+
+
+def test_exports_every_declared_symbol(lib):
+    syms = header_symbols()
+    assert "pm_build" in syms and "pm_scan" in syms and "pm_scan_batch" in syms
+    for s in syms:
+        assert hasattr(lib, s), s
+    assert sorted(pm.EXPORTS) == syms
+
+
+def test_strerror_and_last_error(lib):
+    for code in range(0, -11, -1):
+        assert pm.pm_strerror(code) not in ("", "unknown error")
+    with pytest.raises(pm.PMError) as e:
+        pm.pm_build_host([b"ab", b""])
+    assert e.value.code == pm.PM_ERR_EMPTY_PATTERN
+    assert pm.pm_last_error() == pm.PM_ERR_EMPTY_PATTERN
+    with pytest.raises(pm.PMError) as e:
+        pm.pm_build_host([b"x" * (pm.PM_MAX_PATTERN_LEN + 1)])
+    assert e.value.code == pm.PM_ERR_PATTERN_TOO_LONG
+
+
+def csr_walk(row_ptr, col, nxt, fin, text):
+    """Pure-Python PFAC walk over exported CRS arrays (tiny inputs)."""
+    best_ids, count = [], 0
+    for i in range(len(text)):
+        v, best, j = 0, -1, i
+        while j < len(text):
+            r0, r1 = int(row_ptr[v]), int(row_ptr[v + 1])
+            hit = [e for e in range(r0, r1) if col[e] == text[j]]
+            if not hit:
+                break
+            v = int(nxt[hit[0]])
+            j += 1
+            if fin[v] >= 0:
+                count += 1
+                best = int(fin[v])
+        best_ids.append(best)
+    return best_ids, count
+
+
+@pytest.mark.parametrize("seed,alphabet,npat,lo,hi", [
+    (0, 2, 20, 1, 7), (1, 4, 60, 2, 9), (2, 26, 80, 3, 12), (3, 256, 100, 1, 6)])
+def test_crs_against_oracle(lib, seed, alphabet, npat, lo, hi):
+    wl = W.random_case(seed, npat, 3000, alphabet, lo, hi)
+    pats = wl.patterns.as_list() + [wl.patterns.get(0)]     # one duplicate
+    t = pm.pm_build_host(pats)
+    st = pm.pm_stats(t)
+    ot = oracle.Trie(pats)
+    n, nnz = st["n_nodes"], st["nnz"]
+    # trie shape equals the oracle's independent pointer trie
+    assert n == ot.n_nodes and nnz == ot.n_edges == n - 1
+    assert st["n_patterns"] == len(set(pats)) and st["n_duplicates"] == 1
+    assert st["max_len"] == max(map(len, pats)) and st["min_len"] == min(map(len, pats))
+    # storage formulas: CRS element count 2nnz+n+1 (Section III); 36-byte
+    # bitmapped node and 256-wide state table (Section V)
+    assert st["crs_elements"] == 2 * nnz + n + 1
+    assert st["csr_bytes"] == 4 * (n + 1) + nnz + 4 * nnz + 4 * n
+    assert st["dense256_bytes"] == 256 * 4 * n
+    assert st["bitmap36_bytes"] == 36 * n
+    row_ptr, col, nxt, fin = pm.pm_export_csr(t)
+    # CRS invariants
+    assert row_ptr[0] == 0 and row_ptr[-1] == nnz
+    assert np.all(np.diff(row_ptr.astype(np.int64)) >= 0)
+    for v in range(n):
+        r = col[row_ptr[v]:row_ptr[v + 1]].astype(int)
+        assert np.all(np.diff(r) > 0)
+    # BFS numbering: the e-th non-zero in row order leads to node e+1
+    assert np.array_equal(nxt, np.arange(1, nnz + 1))
+    assert sorted(np.diff(row_ptr.astype(np.int64)).tolist()) == sorted(ot.degrees().tolist())
+    assert int((fin >= 0).sum()) == len(set(pats))
+    # walking the exported CRS gives the oracle's answer
+    text = wl.text.tobytes()[:600]
+    ids, cnt = csr_walk(row_ptr, col, nxt, fin, text)
+    o_ids, o_cnt, _ = ot.scan(text)
+    assert ids == o_ids.tolist() and cnt == o_cnt
+
+
+def test_classes_and_dense_levels(lib):
+    t = pm.pm_build_host([b"ACGTACGTAC", b"ACGGA" * 3, b"TTTTTTTT"])
+    st = pm.pm_stats(t)
+    assert st["alphabet"] == 5           # A, C, G, T + any other byte
+    assert 1 <= st["dense_k_max"] <= st["min_len"]
+    t = pm.pm_build_host([bytes([b]) * 3 for b in range(256)])
+    assert pm.pm_stats(t)["alphabet"] == 256
+
+
+def test_empty_set_and_host_only_scan(lib):
+    t = pm.pm_build_host([])
+    st = pm.pm_stats(t)
+    assert st["n_nodes"] == 1 and st["nnz"] == 0 and st["n_patterns"] == 0
+    import ctypes as C
+    res = pm.pm_result(None, None)
+    rc = lib.pm_scan(t.handle, None, 0, res, None)
+    assert rc == pm.PM_ERR_INVAL or rc == pm.PM_ERR_HOST_ONLY
+    cnt = C.c_int64()
+    rc = lib.pm_scan_ex(t.handle, None, None, 1, 0, None, C.addressof(cnt), None, None, None)
+    assert rc == pm.PM_ERR_HOST_ONLY
+
+
+def test_config_validation(lib):
+    t = pm.pm_build_host([b"hello", b"world"])
+    cfg = pm.pm_get_config(t)
+    assert cfg["threads"] in (128, 256, 512) and cfg["tile"] % (4 * cfg["threads"]) == 0
+    pm.pm_set_config(t, cfg)
+    for bad in ({"threads": 100}, {"tile": 1000}, {"dense_k": 0}, {"stages": 9},
+                {"dense_k": 99}):
+        c = dict(cfg, **bad)
+        with pytest.raises(pm.PMError) as e:
+            pm.pm_set_config(t, c)
+        assert e.value.code == pm.PM_ERR_INVAL

@@ -1,0 +1,352 @@
+"""GPU parity: the CUDA scan through the C ABI against the CPU oracle.
+
+Integer work, so the bar is bit-exact: every ids[i] and every count equal
+the oracle's on the same seeded input. Small cases compare every position;
+the full-size workloads (in the launch configuration the benchmark times)
+compare sampled windows position by position plus the total count.
+"""
+import os
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle
+from paper_1702_03657_gb300 import pm
+from paper_1702_03657_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+HOST_THREADS = max(1, min(16, os.cpu_count() or 1))
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1702_03657_gb300 import build as B
+    B.build()
+    pm.load()
+    torch.cuda.init()
+    yield
+    torch.cuda.synchronize()
+    assert pm.pm_device_error() == 0
+
+
+def dev(a, dtype=torch.uint8):
+    t = torch.from_numpy(np.ascontiguousarray(a))
+    return t.to("cuda")
+
+
+def gpu_scan(trie, text: np.ndarray, cfg=None, lookups=False, offset=0):
+    """Scan through pm_scan (or pm_scan_ex with a config / lookup counter).
+    `offset` shifts the text inside its buffer to test unaligned pointers."""
+    n = len(text)
+    buf = torch.zeros(n + offset + 16, dtype=torch.uint8, device="cuda")
+    if n:
+        buf[offset:offset + n] = dev(text)
+    tv = buf[offset:offset + n]
+    ids = torch.full((n,), -7, dtype=torch.int32, device="cuda")
+    cnt = torch.full((1,), -7, dtype=torch.int64, device="cuda")
+    if cfg is None and not lookups:
+        pm.pm_scan(trie, tv, ids, cnt, length=n)
+        look = None
+    else:
+        lk = torch.zeros(1, dtype=torch.int64, device="cuda") if lookups else None
+        pm.pm_scan_ex(trie, tv, None, ids, cnt, lookups=lk, cfg=cfg, length=n)
+        look = int(lk.item()) if lookups else None
+    torch.cuda.synchronize()
+    return ids.cpu().numpy(), int(cnt.item()), look
+
+
+def assert_same(ids, cnt, o_ids, o_cnt):
+    bad = np.flatnonzero(ids != o_ids)
+    assert bad.size == 0, f"{bad.size} mismatches, first at {bad[:5]}: " \
+                          f"gpu {ids[bad[:5]]} oracle {o_ids[bad[:5]]}"
+    assert cnt == o_cnt
+
+
+def small_cfg(trie, **kw):
+    c = pm.pm_get_config(trie)
+    c.update(threads=128, tile=1024, stages=2)
+    c.update(kw)
+    return c
+
+
+# --------------------------------------------------------------------------
+
+
+def test_golden_fixtures():
+    import glob
+    import json
+    for f in sorted(glob.glob(os.path.join(os.path.dirname(__file__), "golden", "*.json"))):
+        c = json.load(open(f))
+        pats = [bytes.fromhex(p) for p in c["patterns"]]
+        text = np.frombuffer(bytes.fromhex(c["text"]), np.uint8)
+        t = pm.pm_build(pats)
+        ids, cnt, look = gpu_scan(t, text, lookups=True)
+        assert ids.tolist() == c["ids"], f
+        assert cnt == c["count"], f
+        assert look == c["lookups"], f
+        ids2, cnt2, _ = gpu_scan(t, text)
+        assert ids2.tolist() == c["ids"] and cnt2 == c["count"], f
+
+
+@pytest.mark.parametrize("seed,alphabet,npat,lo,hi,n", [
+    (0, 2, 20, 1, 7, 50_001), (1, 3, 60, 1, 9, 70_003), (2, 4, 200, 2, 12, 65_537),
+    (3, 26, 300, 3, 16, 100_000), (4, 256, 500, 1, 8, 99_999), (5, 5, 100, 4, 30, 33_333),
+])
+def test_random_small_all_positions(seed, alphabet, npat, lo, hi, n):
+    wl = W.random_case(seed, npat, n, alphabet, lo, hi, plant_rate=0.05)
+    t = pm.pm_build(wl.patterns)
+    o_ids, o_cnt, o_look = oracle.Trie(wl.patterns).scan(wl.text)
+    ids, cnt, _ = gpu_scan(t, wl.text)                         # default config
+    assert_same(ids, cnt, o_ids, o_cnt)
+    ids, cnt, look = gpu_scan(t, wl.text, cfg=small_cfg(t), lookups=True)
+    assert_same(ids, cnt, o_ids, o_cnt)
+    assert look == o_look
+
+
+def test_config_sweep():
+    """Every launch configuration gives the same bits."""
+    wl = W.random_case(11, 400, 40_000 + 77, 4, 3, 14, plant_rate=0.05)
+    t = pm.pm_build(wl.patterns)
+    st = pm.pm_stats(t)
+    o_ids, o_cnt, _ = oracle.Trie(wl.patterns).scan(wl.text)
+    base = pm.pm_get_config(t)
+    for threads in (128, 256, 512):
+        for tile in (4 * threads, 8192):
+            for k in sorted({1, 2, st["dense_k_max"]}):
+                for cm in (0, 1):
+                    for rs in (0, 1):
+                        for stages in (2, 4):
+                            c = dict(base, threads=threads, tile=tile, dense_k=k,
+                                     childmask=cm, row_search=rs, stages=stages,
+                                     checked=int(threads == 256))
+                            try:
+                                pm.pm_set_config(t, c)
+                            except pm.PMError:
+                                continue  # e.g. no child filter at this k
+                            ids, cnt, _ = gpu_scan(t, wl.text, cfg=c)
+                            assert_same(ids, cnt, o_ids, o_cnt)
+    assert pm.pm_device_error() == 0
+
+
+def test_unaligned_and_ragged():
+    wl = W.random_case(12, 200, 30_011, 26, 2, 20)
+    t = pm.pm_build(wl.patterns)
+    o_ids, o_cnt, _ = oracle.Trie(wl.patterns).scan(wl.text)
+    for off in (1, 3, 8, 15):
+        ids, cnt, _ = gpu_scan(t, wl.text, offset=off)
+        assert_same(ids, cnt, o_ids, o_cnt)
+    # ids pointer not 16-byte aligned
+    tv = dev(wl.text)
+    big = torch.zeros(len(wl.text) + 1, dtype=torch.int32, device="cuda")
+    ids = big[1:]
+    cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
+    pm.pm_scan(t, tv, ids, cnt)
+    torch.cuda.synchronize()
+    assert_same(ids.cpu().numpy(), int(cnt.item()), o_ids, o_cnt)
+    # lengths around tile and halo boundaries
+    c = small_cfg(t)
+    for n in (0, 1, 2, 3, 4, 5, 15, 16, 17, 1023, 1024, 1025, 1024 + 19, 2048, 4097):
+        o_ids2, o_cnt2, _ = oracle.Trie(wl.patterns).scan(wl.text[:n])
+        ids, cnt, _ = gpu_scan(t, wl.text[:n], cfg=c)
+        assert_same(ids, cnt, o_ids2, o_cnt2)
+
+
+def test_degenerate_pattern_sets():
+    rng = np.random.Generator(np.random.MT19937(5))
+    text = rng.integers(0, 256, size=20_000, dtype=np.uint8)
+    text[100:108] = np.frombuffer(b"\x00\x00\xff\xffabcd", np.uint8)
+    cases = [
+        [],                                              # nothing matches
+        [bytes([b]) for b in range(256)],                # every byte, k = 1
+        [b"\x00", b"\x00\x00", b"\xff\xff", b"abcd"],    # NUL and 0xFF
+        [bytes(text[500:500 + 4096])],                    # longest allowed
+        [b"a" * k for k in range(1, 40)],                 # nested prefixes
+        [bytes(text[7:9]), bytes(text[7:9])],             # duplicates
+    ]
+    for pats in cases:
+        t = pm.pm_build(pats)
+        o_ids, o_cnt, o_look = oracle.Trie(pats).scan(text)
+        for cfg in (None, small_cfg(t)):
+            ids, cnt, _ = gpu_scan(t, text, cfg=cfg)
+            assert_same(ids, cnt, o_ids, o_cnt)
+        _, _, look = gpu_scan(t, text, lookups=True)
+        assert look == o_look
+
+
+def test_tiny_config_full():
+    wl = W.tiny(0)
+    t = pm.pm_build(wl.patterns)
+    o_ids, o_cnt, _ = oracle.Trie(wl.patterns).scan(wl.text, threads=HOST_THREADS)
+    ids, cnt, _ = gpu_scan(t, wl.text)
+    assert_same(ids, cnt, o_ids, o_cnt)
+    assert cnt >= 256  # one plant per 4 KiB block
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_paper_scale_reduced_full(seed):
+    wl = W.paper_scale(seed, text_bytes=6 * W.MiB + 13)
+    t = pm.pm_build(wl.patterns)
+    o_ids, o_cnt, _ = oracle.Trie(wl.patterns).scan(wl.text, threads=HOST_THREADS)
+    ids, cnt, _ = gpu_scan(t, wl.text)
+    assert_same(ids, cnt, o_ids, o_cnt)
+
+
+def test_acgt_reduced_full():
+    wl = W.acgt(0, text_bytes=4 * W.MiB + 5, n_patterns=100_000)
+    t = pm.pm_build(wl.patterns)
+    o_ids, o_cnt, o_look = oracle.Trie(wl.patterns).scan(wl.text, threads=HOST_THREADS)
+    ids, cnt, _ = gpu_scan(t, wl.text)
+    assert_same(ids, cnt, o_ids, o_cnt)
+    _, _, look = gpu_scan(t, wl.text, lookups=True)
+    assert look == o_look
+
+
+def batch_gpu(trie, wl, cfg=None):
+    tx = dev(wl.text)
+    off = dev(wl.offsets.astype(np.int64))
+    ids = torch.full((len(wl.text),), -7, dtype=torch.int32, device="cuda")
+    counts = torch.full((wl.ntexts,), -7, dtype=torch.int64, device="cuda")
+    if cfg is None:
+        pm.pm_scan_batch(trie, tx, off, ids, counts)
+    else:
+        pm.pm_scan_ex(trie, tx, off, ids, counts, cfg=cfg)
+    torch.cuda.synchronize()
+    return ids.cpu().numpy(), counts.cpu().numpy()
+
+
+def test_batched_config_full():
+    wl = W.batched(0)
+    t = pm.pm_build(wl.patterns)
+    o_ids, o_counts, _ = oracle.Trie(wl.patterns).scan_batch(wl.text, wl.offsets,
+                                                             threads=1)
+    ids, counts = batch_gpu(t, wl)
+    assert np.array_equal(ids, o_ids)
+    assert np.array_equal(counts, o_counts)
+    ids, counts = batch_gpu(t, wl, cfg=small_cfg(t))
+    assert np.array_equal(ids, o_ids) and np.array_equal(counts, o_counts)
+
+
+def test_batch_edge_cases():
+    pats = [b"abc", b"bc", b"c", b"cab"]
+    texts = [b"", b"ab", b"cabc", b"", b"c", b"abcabc" * 300, b"", b"b"]
+    data, off = W.concat([np.frombuffer(x, np.uint8) for x in texts])
+    wl = W.Workload("edge", 0, W.PatternSet.from_list(pats), data, off)
+    t = pm.pm_build(pats)
+    o_ids, o_counts, _ = oracle.Trie(pats).scan_batch(data, off)
+    for cfg in (None, small_cfg(t)):
+        ids, counts = batch_gpu(t, wl, cfg)
+        assert np.array_equal(ids, o_ids) and np.array_equal(counts, o_counts)
+
+
+def test_batch_graph_capture_and_streams():
+    wl = W.batched(3, ntexts=512, n_patterns=2000)
+    t = pm.pm_build(wl.patterns)
+    o_ids, o_counts, _ = oracle.Trie(wl.patterns).scan_batch(wl.text, wl.offsets)
+    tx = dev(wl.text)
+    off = dev(wl.offsets.astype(np.int64))
+    ids = torch.empty(len(wl.text), dtype=torch.int32, device="cuda")
+    counts = torch.empty(wl.ntexts, dtype=torch.int64, device="cuda")
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        pm.pm_scan_batch(t, tx, off, ids, counts)   # warm-up outside capture
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        pm.pm_scan_batch(t, tx, off, ids, counts)
+    for _ in range(3):
+        ids.fill_(-9)
+        counts.fill_(-9)
+        g.replay()
+        torch.cuda.synchronize()
+        assert np.array_equal(ids.cpu().numpy(), o_ids)
+        assert np.array_equal(counts.cpu().numpy(), o_counts)
+    # two streams scanning different texts with the same handle at once
+    wl2 = W.random_case(9, 100, 300_000, 256, 1, 6)
+    t2 = pm.pm_build(wl.patterns)
+    tx2 = dev(wl2.text)
+    ids2 = torch.empty(len(wl2.text), dtype=torch.int32, device="cuda")
+    c2 = torch.empty(1, dtype=torch.int64, device="cuda")
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+    for _ in range(4):
+        with torch.cuda.stream(s1):
+            pm.pm_scan_batch(t, tx, off, ids, counts)
+        with torch.cuda.stream(s2):
+            pm.pm_scan(t2, tx2, ids2, c2)
+    torch.cuda.synchronize()
+    o2, oc2, _ = oracle.Trie(wl.patterns).scan(wl2.text)
+    assert np.array_equal(ids.cpu().numpy(), o_ids)
+    assert np.array_equal(ids2.cpu().numpy(), o2) and int(c2.item()) == oc2
+
+
+def test_scan_host_chunks():
+    """pm_scan_host cuts the text into chunks that overlap by max_len-1; a
+    match straddling the chunk boundary must be found."""
+    pats = W.paper_scale(0, text_bytes=16, n_patterns=2000).patterns
+    rng = np.random.Generator(np.random.MT19937(3))
+    n = 70 * W.MiB + 123
+    text = rng.integers(0, 256, size=n, dtype=np.uint8)
+    p = np.frombuffer(pats.get(0), np.uint8)
+    for cut in (32 * W.MiB, 64 * W.MiB):
+        text[cut - len(p) // 2: cut - len(p) // 2 + len(p)] = p
+    t = pm.pm_build(pats)
+    h_text = torch.from_numpy(text).pin_memory()
+    h_ids = torch.empty(n, dtype=torch.int32).pin_memory()
+    cnt = pm.pm_scan_host(t, h_text.numpy(), h_ids.numpy())
+    ids_d, cnt_d, _ = gpu_scan(t, text)
+    assert cnt == cnt_d
+    assert np.array_equal(h_ids.numpy(), ids_d)
+    ot = oracle.Trie(pats)
+    for cut in (32 * W.MiB, 64 * W.MiB):
+        a, b = cut - 5000, cut + 5000
+        o_ids, _, _ = ot.scan(text, a, b)
+        assert np.array_equal(h_ids.numpy()[a:b], o_ids)
+        assert h_ids.numpy()[cut - len(p) // 2] >= 0
+
+
+# --------------------------------------------------------------------------
+# full-size workloads, launch configuration of the benchmark
+
+
+def sampled_windows(n, k, w, seed):
+    rng = np.random.Generator(np.random.MT19937(seed))
+    starts = np.sort(rng.integers(0, max(n - w, 1), size=k))
+    return [(int(s), int(min(n, s + w))) for s in starts] + [(max(0, n - w), n)]
+
+
+def check_windows(ot, text, ids, windows):
+    for a, b in windows:
+        o_ids, _, _ = ot.scan(text, a, b)
+        bad = np.flatnonzero(ids[a:b] != o_ids)
+        assert bad.size == 0, f"window {a}: {bad.size} mismatches"
+
+
+def test_paper_scale_full_size():
+    wl = W.paper_scale(0)
+    t = pm.pm_build(wl.patterns)
+    ids, cnt, _ = gpu_scan(t, wl.text)
+    ot = oracle.Trie(wl.patterns)
+    check_windows(ot, wl.text, ids, sampled_windows(len(wl.text), 48, 4096, 1))
+    # positions with a match must hold the oracle's longest id
+    hits = np.flatnonzero(ids >= 0)
+    assert hits.size >= 4096
+    sel = hits[:: max(1, hits.size // 2000)]
+    for i in sel[:2000]:
+        o, _, _ = ot.scan(wl.text, int(i), int(i) + 1)
+        assert o[0] == ids[i]
+    _, o_cnt, _ = ot.scan(wl.text, threads=HOST_THREADS)
+    assert cnt == o_cnt
+
+
+def test_acgt_full_size():
+    wl = W.acgt(0)
+    t = pm.pm_build(wl.patterns)
+    ids, cnt, _ = gpu_scan(t, wl.text)
+    ot = oracle.Trie(wl.patterns)
+    check_windows(ot, wl.text, ids, sampled_windows(len(wl.text), 32, 4096, 2))
+    _, o_cnt, _ = ot.scan(wl.text, threads=HOST_THREADS)
+    assert cnt == o_cnt
