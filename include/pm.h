@@ -77,7 +77,7 @@ typedef struct {
     uint32_t max_len;        /* longest pattern = trie depth                    */
     uint32_t alphabet;       /* byte classes C: bytes used by patterns, +1 for  */
                              /* "any other byte" unless all 256 are used        */
-    uint32_t dense_k_max;    /* deepest dense prefix table built                */
+    uint32_t dense_k_max;    /* deepest level with shared-memory tables         */
     uint64_t crs_elements;   /* 2*nnz + n + 1 (Section III's storage count)     */
     uint64_t csr_bytes;      /* row_ptr u32[n+1] + col u8[nnz] + next i32[nnz]  */
                              /* + final_id i32[n]                               */
@@ -86,17 +86,18 @@ typedef struct {
     uint64_t device_bytes;   /* everything the handle holds on the device      */
 } pm_trie_stats;
 
-/* Launch configuration of the scan kernel (picked by an autotuner). */
+/* Launch configuration of the scan kernel (picked by an autotuner). Every
+ * warp of a CTA is an independent pipeline over its own text tiles. */
 typedef struct {
     int32_t threads;      /* threads per CTA: 128, 256, 512 or 1024           */
-    int32_t tile;         /* text bytes per tile: multiple of 4*threads, <= 64 KiB */
-    int32_t dense_k;      /* trie levels resolved by the dense prefix table,  */
-                          /* 1 .. dense_k_max                                 */
-    int32_t childmask;    /* 1: test a 32-bit child filter of the depth-k     */
-                          /* node before walking its CRS row                  */
+    int32_t tile;         /* text bytes per warp tile: multiple of 128,       */
+                          /* 128 .. 32768                                     */
+    int32_t dense_k;      /* trie levels resolved in shared memory before a   */
+                          /* CRS walk: 0 .. dense_k_max (< shortest pattern)  */
+    int32_t filter_bits;  /* child-filter width per k-gram: 8, 16 or 32       */
     int32_t row_search;   /* 0: linear, 1: binary search of the byte column   */
     int32_t ctas_per_sm;  /* persistent grid = SMs * ctas_per_sm (0: maximum) */
-    int32_t stages;       /* text tiles in flight per CTA (TMA), 2..4         */
+    int32_t stages;       /* tiles in flight per warp (TMA), 2..4             */
     int32_t checked;      /* 1: bounds-checked scan (PM_ERR_BOUNDS on error)  */
 } pm_config;
 

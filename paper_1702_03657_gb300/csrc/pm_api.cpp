@@ -51,50 +51,71 @@ int max_smem_optin(int device)
     return v;
 }
 
-// Default launch configuration: the deepest dense table, the child filter
-// when it exists, three tiles in flight; shrunk until it fits the SM.
+int width_index(int32_t bits) { return bits == 8 ? 0 : bits == 16 ? 1 : bits == 32 ? 2 : -1; }
+
+bool have_filter(const pm_trie *h, int32_t k, int32_t bits)
+{
+    const int wi = width_index(bits);
+    return k >= 0 && (uint32_t)k <= h->host.dense_k_max && wi >= 0 && !h->host.filter[k][wi].empty();
+}
+
+// Narrowest filter that is exact at this level (C <= W), else the widest
+// that exists, else 0.
+int32_t pick_bits(const pm_trie *h, int32_t k)
+{
+    for (int32_t b : {8, 16, 32})
+        if ((uint32_t)b >= h->host.C && have_filter(h, k, b)) return b;
+    for (int32_t b : {8, 16, 32})
+        if (have_filter(h, k, b)) return b;
+    return 0;
+}
+
+// Default launch configuration: 32 independent warps per CTA with 2 KiB
+// warp tiles double-buffered and the deepest filter level; shrunk until it
+// fits the SM.
 pm_config default_config(const pm_trie *h, int smem_limit)
 {
     pm_config c{};
-    c.threads = 512;
-    c.tile = 16384;
+    c.threads = 1024;
+    c.tile = 2048;
     c.dense_k = (int32_t)h->host.dense_k_max;
-    c.childmask = h->host.childmask[c.dense_k].empty() ? 0 : 1;
+    c.filter_bits = pick_bits(h, c.dense_k);
     c.row_search = 0;
     c.ctas_per_sm = 0;
-    c.stages = 3;
+    c.stages = 2;
     c.checked = 0;
-    // static shared memory of the kernel (reduction scratch) + slack
     const uint64_t limit = (uint64_t)smem_limit - 1024;
     while (pm::scan_smem_bytes(h->dev, c) > limit) {
-        if (c.stages > 2) c.stages = 2;
-        else if (c.tile > 4 * c.threads) c.tile /= 2;
-        else if (c.childmask) c.childmask = 0;
-        else if (c.dense_k > 1) {
+        if (c.threads > 512) c.threads /= 2;
+        else if (c.tile > 1024) c.tile /= 2;
+        else if (c.dense_k > 0) {
             --c.dense_k;
-            c.childmask = h->host.childmask[c.dense_k].empty() ? 0 : 1;
-            c.tile = 16384;
-        } else break;
+            c.filter_bits = pick_bits(h, c.dense_k);
+            c.threads = 1024;
+            c.tile = 2048;
+        } else if (c.threads > 128) c.threads /= 2;
+        else if (c.tile > 128) c.tile /= 2;
+        else break;
     }
     return c;
 }
 
 int validate_config(const pm_trie *h, const pm_config &c, std::string &why)
 {
-    if (c.threads != 128 && c.threads != 256 && c.threads != 512) {
-        why = "threads must be 128, 256 or 512";
+    if (c.threads != 128 && c.threads != 256 && c.threads != 512 && c.threads != 1024) {
+        why = "threads must be 128, 256, 512 or 1024";
         return PM_ERR_INVAL;
     }
-    if (c.tile < 4 * c.threads || c.tile > 65536 || c.tile % (4 * c.threads) != 0) {
-        why = "tile must be a multiple of 4*threads in [4*threads, 65536]";
+    if (c.tile < 128 || c.tile > 32768 || c.tile % 128 != 0) {
+        why = "tile must be a multiple of 128 in [128, 32768]";
         return PM_ERR_INVAL;
     }
-    if (c.dense_k < 1 || (uint32_t)c.dense_k > h->host.dense_k_max) {
-        why = "dense_k must be in 1..dense_k_max";
+    if (c.dense_k < 0 || (uint32_t)c.dense_k > h->host.dense_k_max) {
+        why = "dense_k must be in 0..dense_k_max";
         return PM_ERR_INVAL;
     }
-    if (c.childmask && h->host.childmask[c.dense_k].empty()) {
-        why = "no child filter table at this dense_k";
+    if (!have_filter(h, c.dense_k, c.filter_bits)) {
+        why = "no filter of this width at this dense_k (widths 8, 16, 32)";
         return PM_ERR_INVAL;
     }
     if (c.stages < 2 || c.stages > 4) {
@@ -105,9 +126,8 @@ int validate_config(const pm_trie *h, const pm_config &c, std::string &why)
         why = "ctas_per_sm must be 0..32";
         return PM_ERR_INVAL;
     }
-    if (c.row_search < 0 || c.row_search > 1 || c.checked < 0 || c.checked > 1 ||
-        c.childmask < 0 || c.childmask > 1) {
-        why = "row_search, childmask and checked are 0 or 1";
+    if (c.row_search < 0 || c.row_search > 1 || c.checked < 0 || c.checked > 1) {
+        why = "row_search and checked are 0 or 1";
         return PM_ERR_INVAL;
     }
     uint64_t need = pm::scan_smem_bytes(h->dev, c);
@@ -133,6 +153,8 @@ void fill_dev_sizes(pm_trie *h)
         d.dense_words[k] = (uint32_t)(t.dense[k].size() / 2);
         d.first[k] = t.first[k];
         d.nlevel[k] = t.nlevel[k];
+        for (int w = 0; w < pm::kFilterWidths; ++w)
+            d.filter_words[k][w] = (uint32_t)t.filter[k][w].size();
     }
 }
 
@@ -159,12 +181,14 @@ int upload(pm_trie *h)
     size_t i_next = add(t.next.data(), 4 * nnz);
     size_t i_emit = add(emit.data(), 8 * n);
     size_t i_cls = add(t.cls, 256);
-    size_t i_dense[pm::kMaxDenseK + 1] = {};
-    size_t i_cm[pm::kMaxDenseK + 1] = {};
-    for (int k = 1; k <= pm::kMaxDenseK; ++k) {
-        i_dense[k] = t.dense[k].empty() ? (size_t)-1 : add(t.dense[k].data(), 4 * t.dense[k].size());
-        i_cm[k] = t.childmask[k].empty() ? (size_t)-1
-                                         : add(t.childmask[k].data(), 4 * t.childmask[k].size());
+    const size_t none = (size_t)-1;
+    size_t i_dense[pm::kMaxDenseK + 1];
+    size_t i_f[pm::kMaxDenseK + 1][pm::kFilterWidths];
+    for (int k = 0; k <= pm::kMaxDenseK; ++k) {
+        i_dense[k] = t.dense[k].empty() ? none : add(t.dense[k].data(), 4 * t.dense[k].size());
+        for (int w = 0; w < pm::kFilterWidths; ++w)
+            i_f[k][w] = t.filter[k][w].empty() ? none
+                                               : add(t.filter[k][w].data(), 4 * t.filter[k][w].size());
     }
     cudaError_t e = cudaGetDevice(&h->device);
     if (e != cudaSuccess) return cuda_fail("cudaGetDevice", e);
@@ -190,12 +214,13 @@ int upload(pm_trie *h)
     d.next = reinterpret_cast<const int32_t *>(base + parts[i_next].off);
     d.emit = reinterpret_cast<const int2 *>(base + parts[i_emit].off);
     d.cls = base + parts[i_cls].off;
-    for (int k = 1; k <= pm::kMaxDenseK; ++k) {
-        d.dense[k] = i_dense[k] == (size_t)-1 ? nullptr
-                                              : reinterpret_cast<const uint2 *>(base + parts[i_dense[k]].off);
-        d.childmask[k] = i_cm[k] == (size_t)-1
-                             ? nullptr
-                             : reinterpret_cast<const uint32_t *>(base + parts[i_cm[k]].off);
+    for (int k = 0; k <= pm::kMaxDenseK; ++k) {
+        d.dense[k] = i_dense[k] == none ? nullptr
+                                        : reinterpret_cast<const uint2 *>(base + parts[i_dense[k]].off);
+        for (int w = 0; w < pm::kFilterWidths; ++w)
+            d.filter[k][w] = i_f[k][w] == none
+                                 ? nullptr
+                                 : reinterpret_cast<const uint32_t *>(base + parts[i_f[k][w]].off);
     }
     return PM_OK;
 }

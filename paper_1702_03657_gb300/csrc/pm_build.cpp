@@ -175,30 +175,35 @@ int build_host_trie(const uint8_t *const *patterns, const uint32_t *lengths,
     }
     const uint32_t nn = (uint32_t)rng.size();
 
-    // Dense prefix tables for k = 1 .. K: the first k levels over the classes.
-    // k never exceeds the shortest pattern, so a walk that ends inside the
-    // table (a k-gram with no root path) has matched nothing.
+    // Top-level tables for k = 0 .. K, K < shortest pattern, so that no
+    // pattern ends within the levels a table resolves.
     for (int k = 0; k <= kMaxDenseK; ++k) {
         t.dense[k].clear();
-        t.childmask[k].clear();
+        for (int w = 0; w < kFilterWidths; ++w) t.filter[k][w].clear();
         t.first[k] = t.nlevel[k] = 0;
     }
-    uint32_t kcap = m ? std::min<uint32_t>(t.min_len, kMaxDenseK) : 1;
-    const uint64_t max_codes = kDenseBudget / 8 * 32;
+    const uint32_t kcap = m ? std::min<uint32_t>(t.min_len - 1, kMaxDenseK) : 0;
+    const uint64_t max_codes = kFilterBudget;  // C^k * 8 bits <= budget
     uint32_t K = 0;
     for (uint32_t k = 1; k <= kcap; ++k) {
-        uint64_t codes = ipow_capped(t.C, (int)k, max_codes);
-        if (codes == 0) break;
+        if (ipow_capped(t.C, (int)k, max_codes) == 0) break;
         K = k;
     }
-    if (K == 0) K = 1;  // C^1 <= 256 always fits
     t.dense_k_max = K;
 
-    std::vector<uint64_t> code(nn, 0);
+    // code: base-C code of a node's path (first byte most significant), the
+    // order in which BFS numbers each level. With the byte alphabet the
+    // filter is indexed instead by the little-endian path (first byte least
+    // significant), which the kernel reads straight from the text.
+    const bool le = t.C == 256;
+    std::vector<uint64_t> code(nn, 0), fcode(nn, 0);
     for (uint32_t v = 0; v < nn; ++v) {
         if (t.depth[v] >= K) continue;
-        for (uint32_t e = t.row_ptr[v]; e < t.row_ptr[v + 1]; ++e)
+        for (uint32_t e = t.row_ptr[v]; e < t.row_ptr[v + 1]; ++e) {
             code[t.next[e]] = code[v] * t.C + t.cls[t.col[e]];
+            fcode[t.next[e]] = le ? fcode[v] | ((uint64_t)t.col[e] << (8 * t.depth[v]))
+                                  : code[t.next[e]];
+        }
     }
     std::vector<uint32_t> lvl_begin(K + 2, nn), lvl_count(K + 2, 0);
     for (uint32_t v = 0; v < nn; ++v) {
@@ -206,40 +211,48 @@ int build_host_trie(const uint8_t *const *patterns, const uint32_t *lengths,
         if (d > K) break;  // BFS: depths never decrease
         if (lvl_count[d]++ == 0) lvl_begin[d] = v;
     }
-    for (uint32_t k = 1; k <= K; ++k) {
-        uint64_t codes = ipow_capped(t.C, (int)k, ~0ull);
-        uint64_t words = (codes + 31) / 32;
-        words += words & 1;  // even: the table is copied in 16-byte units
-        std::vector<uint32_t> &tab = t.dense[k];
-        tab.assign(2 * words, 0);
+    for (uint32_t k = 0; k <= K; ++k) {
+        const uint64_t codes = ipow_capped(t.C, (int)k, ~0ull);
         t.first[k] = lvl_count[k] ? lvl_begin[k] : 0;
         t.nlevel[k] = lvl_count[k];
-        uint64_t prev = 0;
-        for (uint32_t i = 0; i < lvl_count[k]; ++i) {
-            uint32_t v = lvl_begin[k] + i;
-            uint64_t c = code[v];
-            if (i > 0 && c <= prev) {
-                msg = "internal: depth-k nodes not in code order";
-                return PM_ERR_INVAL;
-            }
-            prev = c;
-            tab[2 * (c >> 5)] |= 1u << (c & 31);
-        }
-        uint32_t run = 0;
-        for (uint64_t w = 0; w < words; ++w) {
-            tab[2 * w + 1] = run;
-            run += (uint32_t)__builtin_popcount(tab[2 * w]);
-        }
-        if ((uint64_t)lvl_count[k] * 4 <= kChildMaskBudget) {
-            std::vector<uint32_t> &cm = t.childmask[k];
-            uint32_t cnt = lvl_count[k] + ((4 - lvl_count[k] % 4) % 4);
-            cm.assign(std::max<uint32_t>(cnt, 4), 0);
+        if (k >= 1) {
+            uint64_t words = (codes + 31) / 32;
+            words += words & 1;  // even: copied in 16-byte units
+            std::vector<uint32_t> &tab = t.dense[k];
+            tab.assign(2 * words, 0);
+            uint64_t prev = 0;
             for (uint32_t i = 0; i < lvl_count[k]; ++i) {
-                uint32_t v = lvl_begin[k] + i;
-                uint32_t mask = 0;
-                for (uint32_t e = t.row_ptr[v]; e < t.row_ptr[v + 1]; ++e)
-                    mask |= 1u << (t.cls[t.col[e]] & 31);
-                cm[i] = mask;
+                const uint64_t c = code[lvl_begin[k] + i];
+                if (i > 0 && c <= prev) {
+                    msg = "internal: depth-k nodes not in code order";
+                    return PM_ERR_INVAL;
+                }
+                prev = c;
+                tab[2 * (c >> 5)] |= 1u << (c & 31);
+            }
+            uint32_t run = 0;
+            for (uint64_t w = 0; w < words; ++w) {
+                tab[2 * w + 1] = run;
+                run += (uint32_t)__builtin_popcount(tab[2 * w]);
+            }
+        }
+        for (int wi = 0; wi < kFilterWidths; ++wi) {
+            const uint32_t W = 8u << wi;
+            const uint64_t bits = codes * W;
+            if (bits / 8 > kFilterBudget) continue;
+            uint64_t words = (bits + 31) / 32;
+            words = (words + 3) & ~3ull;  // 16-byte units
+            std::vector<uint32_t> &f = t.filter[k][wi];
+            f.assign(words, 0);
+            for (uint32_t i = 0; i < lvl_count[k]; ++i) {
+                const uint32_t v = lvl_begin[k] + i;
+                const uint64_t c = fcode[v];
+                for (uint32_t e = t.row_ptr[v]; e < t.row_ptr[v + 1]; ++e) {
+                    const uint64_t h = t.cls[t.col[e]] % W;
+                    // byte alphabet: bit (h << 8k) | path; else: path * W + h
+                    const uint64_t bit = le ? (h << (8 * k)) | c : c * W + h;
+                    f[bit >> 5] |= 1u << (bit & 31);
+                }
             }
         }
     }

@@ -12,12 +12,14 @@
 
 namespace pm {
 
-// Deepest dense prefix table (trie levels resolved by one table lookup).
+// Deepest dense prefix level (trie levels resolved by one table lookup).
 constexpr int kMaxDenseK = 12;
-// Shared-memory budget of one dense table (bitmap + rank words).
-constexpr uint64_t kDenseBudget = 144u * 1024u;
-// Shared-memory budget of one child-filter table (u32 per depth-k node).
-constexpr uint64_t kChildMaskBudget = 96u * 1024u;
+// Budget of one dense (bitmap + rank) table; it is read from global memory.
+constexpr uint64_t kDenseBudget = 1u << 20;
+// Shared-memory budget of one filter table.
+constexpr uint64_t kFilterBudget = 128u * 1024u;
+// Filter widths: W = 8, 16, 32 bits per k-gram (index 0, 1, 2).
+constexpr int kFilterWidths = 3;
 
 // Device view of a built trie; passed by value to the scan kernels.
 //
@@ -30,30 +32,43 @@ constexpr uint64_t kChildMaskBudget = 96u * 1024u;
 // ending on that path. A walk that stops at v has found exactly the nfinal
 // patterns on its path and its longest match is best.
 //
-// Dense prefix table of level k: the first k trie levels expanded over the
-// byte classes. A k-gram of classes (c_0..c_{k-1}) has code
-// sum_j c_j * C^(k-1-j); bit `code` of the table is set iff the k-gram spells
-// a root path, and then the depth-k node it reaches is
-//   first[k] + rank(code) = first[k] + base(word) + popc(word & lower bits),
-// because BFS numbers the depth-k nodes contiguously in code order. The table
-// is stored as uint2 {bits, base} per 32 codes.
+// Byte classes: the bytes used by some pattern, in ascending byte order, then
+// one class for every other byte (none when all 256 are used: class = byte).
+// A k-gram of classes c_0..c_{k-1} has code sum_j c_j * C^(k-1-j).
+//
+// Dense table of level k (global memory): bit `code` is set iff the k-gram
+// spells a root path, and then the depth-k node it reaches is
+//   first[k] + base(word) + popc(word & lower bits),
+// because BFS numbers the depth-k nodes contiguously in code order. Stored
+// as uint2 {bits, base} per 32 codes.
+//
+// Filter of level k and width W (shared memory): a bitset of C^k * W bits.
+// For a k-gram spelling a root path and a next class c_k, the bit
+//   code*W + (c_k mod W)                         (C < 256), or
+//   ((c_k mod W) << 8k) | sum_j b_j << 8j        (byte alphabet, the path
+//                                                 read little-endian)
+// is set iff the depth-k node has a child of some class congruent to c_k
+// mod W; bits of k-grams that are not root paths are clear. It is exact
+// when C <= W. With k < shortest pattern, a clear bit proves that the walk
+// from this start position stops at depth <= k without a match.
 struct TrieDev {
     const uint32_t *row_ptr;
     const uint8_t *col;
     const int32_t *next;
     const int2 *emit;
-    const uint8_t *cls;                    // byte -> class, 256 entries
-    const uint2 *dense[kMaxDenseK + 1];    // index k (0 unused)
-    const uint32_t *childmask[kMaxDenseK + 1];
-    uint32_t dense_words[kMaxDenseK + 1];  // uint2 entries of table k
-    uint32_t first[kMaxDenseK + 1];        // BFS id of the first depth-k node
-    uint32_t nlevel[kMaxDenseK + 1];       // number of depth-k nodes
-    uint32_t C;                            // classes
+    const uint8_t *cls;                                   // byte -> class
+    const uint2 *dense[kMaxDenseK + 1];                   // index k (0 unused)
+    const uint32_t *filter[kMaxDenseK + 1][kFilterWidths];
+    uint32_t filter_words[kMaxDenseK + 1][kFilterWidths]; // u32 words
+    uint32_t dense_words[kMaxDenseK + 1];                 // uint2 entries of table k
+    uint32_t first[kMaxDenseK + 1];                       // BFS id of the first depth-k node
+    uint32_t nlevel[kMaxDenseK + 1];                      // number of depth-k nodes
+    uint32_t C;                                           // classes
     uint32_t n_nodes;
     uint32_t nnz;
-    uint32_t min_len;                      // shortest pattern (>= 1)
+    uint32_t min_len;                                     // shortest pattern (>= 1)
     uint32_t max_len;
-    uint32_t dense_k_max;
+    uint32_t dense_k_max;                                 // deepest filter level
 };
 
 // Host-side trie: the CRS arrays plus the derived tables.
@@ -71,7 +86,7 @@ struct HostTrie {
     uint64_t n_patterns = 0, n_duplicates = 0;
     uint32_t dense_k_max = 0;
     std::vector<uint32_t> dense[kMaxDenseK + 1];     // interleaved {bits, base}
-    std::vector<uint32_t> childmask[kMaxDenseK + 1];
+    std::vector<uint32_t> filter[kMaxDenseK + 1][kFilterWidths];
     uint32_t first[kMaxDenseK + 1] = {};
     uint32_t nlevel[kMaxDenseK + 1] = {};
 };

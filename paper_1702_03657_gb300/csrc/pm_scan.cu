@@ -55,17 +55,24 @@ struct KParams {
     int32_t *ids;
     int64_t *counts;
     unsigned long long *lookups;
+    const uint32_t *filter;     // filter table of level k, width W (global)
+    const uint2 *dense;         // dense table of level k (k >= 1)
+    uint32_t first_k;           // BFS id of the first depth-k node
     uint32_t tile;
     uint32_t halo;
     uint32_t k;
-    uint32_t use_cm;
+    uint32_t lw;                // log2 W
     uint32_t binary;
     uint32_t stages;
     uint32_t aligned;
     uint32_t ids_aligned;
     // shared-memory layout (byte offsets)
-    uint32_t off_cm, off_lut, off_bar, off_stage, stage_bytes;
-    uint32_t dense_u4, cm_u4;   // table sizes in 16-byte units
+    uint32_t off_lut, off_warp;   // shared tables, then per-warp blocks
+    uint32_t warp_bytes;          // bytes of one warp's block
+    uint32_t off_queue, off_stages;  // inside a warp's block (after its mbarriers)
+    uint32_t stage_bytes;         // tile + halo
+    uint32_t filt_u4;             // filter size in 16-byte units
+    uint32_t filt_words;          // filter size in u32 words
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p)
@@ -149,8 +156,8 @@ __device__ __forceinline__ unsigned long long tile_bytes(const KParams &p, unsig
     return left < want ? left : want;
 }
 
-// Issue the TMA copy of tile `tile_idx` into stage `s` (thread 0 only).
-__device__ __forceinline__ void issue_tile(const KParams &p, uint8_t *smem, uint64_t *bars,
+// Issue the TMA copy of tile `tile_idx` into stage `s` of a warp (lane 0).
+__device__ __forceinline__ void issue_tile(const KParams &p, uint8_t *stages, uint64_t *bars,
                                            uint32_t s, unsigned long long tile_idx,
                                            unsigned long long end)
 {
@@ -159,7 +166,7 @@ __device__ __forceinline__ void issue_tile(const KParams &p, uint8_t *smem, uint
     uint32_t nb16 = nb & ~15u;
     if (p.aligned && nb16) {
         mbar_arrive_tx(&bars[s], nb16);
-        tma_load_1d(smem + p.off_stage + (size_t)s * p.stage_bytes, p.text + t0, nb16, &bars[s]);
+        tma_load_1d(stages + (size_t)s * p.stage_bytes, p.text + t0, nb16, &bars[s]);
     } else {
         mbar_arrive(&bars[s]);
     }
@@ -179,87 +186,219 @@ __device__ __forceinline__ uint32_t find_text(const uint64_t *off, uint32_t ntex
     return lo;
 }
 
-template <int KC, bool IDENT, bool BATCH, int MODE>
-__global__ void __launch_bounds__(512) pfac_scan_kernel(const KParams p)
+// Per-warp walk queue: one u32 entry per 4-position group that has at least
+// one position to walk: tile-relative position of the group | mask << 16.
+constexpr int kQueue = 128;  // >= the 32 groups of one warp step
+
+// Walk the CRS rows from node v at staged byte lj until the first mismatch
+// or lj == lim (Section II-C). Returns the deepest node; lj is advanced.
+template <int MODE>
+__device__ __forceinline__ uint32_t crs_walk(const TrieDev &t, const uint8_t *st, uint32_t &lj,
+                                             uint32_t lim, uint32_t v, uint32_t binary,
+                                             unsigned long long &look)
+{
+    while (lj < lim) {
+        const uint32_t b = st[lj];
+        if (MODE == MODE_CHECKED && v >= t.n_nodes) {
+            record_error(PM_ERR_BOUNDS);
+            break;
+        }
+        const uint32_t r0 = __ldg(t.row_ptr + v), r1 = __ldg(t.row_ptr + v + 1);
+        if (MODE == MODE_CHECKED && (r1 < r0 || r1 > t.nnz)) {
+            record_error(PM_ERR_BOUNDS);
+            break;
+        }
+        if (MODE == MODE_LOOKUPS) ++look;
+        if (r1 == r0) break;  // leaf
+        // the first column entry and its next state are fetched together
+        const uint32_t c0 = __ldg(t.col + r0);
+        const uint32_t n0 = (uint32_t)__ldg(t.next + r0);
+        if (c0 == b) {
+            v = n0;
+            ++lj;
+            continue;
+        }
+        if (c0 > b || r1 - r0 == 1) break;
+        uint32_t e;
+        bool found = false;
+        if (binary) {
+            uint32_t lo = r0 + 1, hi = r1;
+            while (lo < hi) {
+                const uint32_t mid = (lo + hi) >> 1;
+                if (__ldg(t.col + mid) < b) lo = mid + 1;
+                else hi = mid;
+            }
+            e = lo;
+            found = lo < r1 && __ldg(t.col + lo) == b;
+        } else {
+            for (e = r0 + 1; e < r1; ++e) {
+                const uint32_t cb = __ldg(t.col + e);
+                if (cb >= b) {
+                    found = cb == b;
+                    break;
+                }
+            }
+        }
+        if (!found) break;
+        v = (uint32_t)__ldg(t.next + e);
+        ++lj;
+    }
+    return v;
+}
+
+// End of the current text relative to the tile start, clipped to 32 bits.
+__device__ __forceinline__ uint32_t rel_end_of(unsigned long long e, unsigned long long t0)
+{
+    const unsigned long long r = e - t0;
+    return r > 0xFFFFFFFFull ? 0xFFFFFFFFu : (uint32_t)r;
+}
+
+// Class of byte b from the lane-replicated LUT (identity for the byte alphabet).
+template <bool IDENT>
+__device__ __forceinline__ uint32_t class_of(const uint32_t *s_lut, uint32_t lane, uint32_t b)
+{
+    if (IDENT) return b;
+    return (s_lut[(b >> 2) * 32 + lane] >> ((b & 3) * 8)) & 0xFFu;
+}
+
+// Phase 2: every lane takes queued groups and walks their flagged positions
+// from the depth-k node (found with the dense table; the filter proved the
+// k-gram is a root path) or, near a text end, from the root. Positions whose
+// walk finds a match get their id patched and their count added.
+template <bool IDENT, bool BATCH, int MODE>
+__device__ __forceinline__ void walk_queue(const KParams &p, const uint32_t *queue, uint32_t qn,
+                                           const uint8_t *st, unsigned long long t0,
+                                           uint32_t nbytes, unsigned long long end, uint32_t k,
+                                           const uint32_t *s_lut, uint32_t lane,
+                                           unsigned long long &acc, unsigned long long &look)
+{
+    const TrieDev &t = p.t;
+    __syncwarp();
+    for (uint32_t j = lane; j < qn; j += 32) {
+        const uint32_t e = queue[j];
+        const uint32_t g0 = e & 0xFFFFu;
+        uint32_t m = e >> 16;
+        uint32_t txt = 0;
+        unsigned long long tend = end;
+        if (BATCH) {
+            txt = find_text(p.offsets, p.ntexts, t0 + g0 + (__ffs(m) - 1));
+            tend = __ldg(p.offsets + txt + 1);
+        }
+        while (m) {
+            const uint32_t q = __ffs(m) - 1;
+            m &= m - 1;
+            const uint32_t lp = g0 + q;
+            const unsigned long long pos = t0 + lp;
+            if (BATCH) {
+                while (pos >= tend) {
+                    ++txt;
+                    tend = __ldg(p.offsets + txt + 1);
+                }
+            }
+            const unsigned long long lim64 = tend - t0;
+            const uint32_t lim = lim64 < nbytes ? (uint32_t)lim64 : nbytes;
+            uint32_t v = 0, lj = lp;
+            if (MODE != MODE_LOOKUPS && k > 0 && pos + k < tend) {
+                uint32_t code = 0;
+                for (uint32_t j2 = 0; j2 < k; ++j2)
+                    code = code * t.C + class_of<IDENT>(s_lut, lane, st[lp + j2]);
+                const uint2 d = __ldg(p.dense + (code >> 5));
+                v = p.first_k + d.y + __popc(d.x & ((1u << (code & 31u)) - 1u));
+                lj = lp + k;
+            }
+            v = crs_walk<MODE>(t, st, lj, lim, v, p.binary, look);
+            if (lj - lp >= t.min_len) {
+                const int2 em = __ldg(t.emit + v);
+                if (em.y) {
+                    p.ids[pos] = em.x;
+                    if (BATCH)
+                        atomicAdd(reinterpret_cast<unsigned long long *>(p.counts + txt),
+                                  (unsigned long long)em.y);
+                    else
+                        acc += (unsigned)em.y;
+                }
+            }
+        }
+    }
+    __syncwarp();
+}
+
+// KF: the filter level k when fixed at compile time (byte alphabet), or -1
+// for a runtime k over byte classes.
+template <int KF, bool IDENT, bool BATCH, int MODE>
+__global__ void __launch_bounds__(1024, 1) pfac_scan_kernel(const KParams p)
 {
     extern __shared__ __align__(16) uint8_t smem[];
     const TrieDev &t = p.t;
-    const uint32_t tid = threadIdx.x, T = blockDim.x, lane = tid & 31;
+    const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const uint32_t NW = blockDim.x >> 5;
 
     const unsigned long long total = BATCH ? __ldg(p.offsets + p.ntexts) : p.total;
     const unsigned long long end = BATCH ? total : p.limit;
     const unsigned long long ntiles = (total + p.tile - 1) / p.tile;
-    if (blockIdx.x >= ntiles) return;
-    const unsigned long long my_tiles = (ntiles - 1 - blockIdx.x) / gridDim.x + 1;
+    if ((unsigned long long)blockIdx.x * NW >= ntiles) return;
 
-    uint2 *s_dense = reinterpret_cast<uint2 *>(smem);
-    uint32_t *s_cm = reinterpret_cast<uint32_t *>(smem + p.off_cm);
+    uint32_t *s_filt = reinterpret_cast<uint32_t *>(smem);
     uint32_t *s_lut = reinterpret_cast<uint32_t *>(smem + p.off_lut);
-    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + p.off_bar);
-    __shared__ uint32_t s_text0;
-    __shared__ unsigned long long s_red[32];
 
-    // Tables into shared memory (once per CTA).
+    // Tables into shared memory, shared by all warps of the CTA.
     {
-        const uint4 *src = reinterpret_cast<const uint4 *>(t.dense[p.k]);
-        uint4 *dst = reinterpret_cast<uint4 *>(s_dense);
-        for (uint32_t i = tid; i < p.dense_u4; i += T) dst[i] = __ldg(src + i);
-        if (p.use_cm) {
-            const uint4 *cs = reinterpret_cast<const uint4 *>(t.childmask[p.k]);
-            uint4 *cd = reinterpret_cast<uint4 *>(s_cm);
-            for (uint32_t i = tid; i < p.cm_u4; i += T) cd[i] = __ldg(cs + i);
-        }
+        const uint4 *src = reinterpret_cast<const uint4 *>(p.filter);
+        uint4 *dst = reinterpret_cast<uint4 *>(s_filt);
+        for (uint32_t i = tid; i < p.filt_u4; i += blockDim.x) dst[i] = __ldg(src + i);
         if (!IDENT) {
             // class LUT replicated per lane: word (b/4)*32 + lane holds the
             // classes of bytes 4*(b/4) .. +3, so lane l always hits bank l.
-            for (uint32_t i = tid; i < 64 * 32; i += T) {
-                uint32_t w = i >> 5;
-                uint32_t v = (uint32_t)__ldg(t.cls + 4 * w) | ((uint32_t)__ldg(t.cls + 4 * w + 1) << 8) |
-                             ((uint32_t)__ldg(t.cls + 4 * w + 2) << 16) |
-                             ((uint32_t)__ldg(t.cls + 4 * w + 3) << 24);
-                s_lut[i] = v;
+            for (uint32_t i = tid; i < 64 * 32; i += blockDim.x) {
+                const uint32_t w = i >> 5;
+                s_lut[i] = (uint32_t)__ldg(t.cls + 4 * w) | ((uint32_t)__ldg(t.cls + 4 * w + 1) << 8) |
+                           ((uint32_t)__ldg(t.cls + 4 * w + 2) << 16) |
+                           ((uint32_t)__ldg(t.cls + 4 * w + 3) << 24);
             }
         }
     }
-    if (tid == 0) {
+    __syncthreads();  // the only CTA-wide barrier: warps run independently below
+
+    const unsigned long long gw = (unsigned long long)blockIdx.x * NW + warp;
+    const unsigned long long TW = (unsigned long long)gridDim.x * NW;
+    if (gw >= ntiles) return;
+    const unsigned long long my_tiles = (ntiles - 1 - gw) / TW + 1;
+
+    uint8_t *wsm = smem + p.off_warp + (size_t)warp * p.warp_bytes;
+    uint64_t *bars = reinterpret_cast<uint64_t *>(wsm);
+    uint32_t *queue = reinterpret_cast<uint32_t *>(wsm + p.off_queue);
+    uint8_t *stages = wsm + p.off_stages;
+
+    if (lane == 0) {
         for (uint32_t s = 0; s < p.stages; ++s) mbar_init(&bars[s], 1);
         fence_mbar_init();
-    }
-    __syncthreads();
-    if (tid == 0) {
-        unsigned long long pre = my_tiles < p.stages ? my_tiles : p.stages;
+        const unsigned long long pre = my_tiles < p.stages ? my_tiles : p.stages;
         for (unsigned long long i = 0; i < pre; ++i)
-            issue_tile(p, smem, bars, (uint32_t)i, blockIdx.x + i * gridDim.x, end);
+            issue_tile(p, stages, bars, (uint32_t)i, gw + i * TW, end);
     }
+    __syncwarp();
 
-    auto cls_of = [&](uint32_t b) -> uint32_t {
-        if (IDENT) return b;
-        return (s_lut[(b >> 2) * 32 + lane] >> ((b & 3) * 8)) & 0xFFu;
-    };
-
-    const uint32_t k = p.k;
+    const uint32_t k = KF >= 0 ? (uint32_t)KF : p.k;
     const uint32_t C = t.C;
-    const uint32_t first_k = t.first[k];
     const uint32_t min_len = t.min_len;
-    unsigned long long acc = 0;       // matches of the current text
-    unsigned long long look = 0;      // lookups (MODE_LOOKUPS)
-    uint32_t cur = 0;                 // current text (batch mode)
+    const uint32_t lw = p.lw;
+    const uint32_t wmask = (1u << lw) - 1u;
+    // IDENT: filter bit index = low 8k+lw bits of the little-endian window
+    const uint32_t imask = KF >= 0 ? (uint32_t)((1ull << (8 * (KF >= 0 ? KF : 0) + lw)) - 1ull) : 0u;
+    unsigned long long acc = 0;   // matches (single text)
+    unsigned long long look = 0;  // lookups (MODE_LOOKUPS)
 
     for (unsigned long long it = 0; it < my_tiles; ++it) {
         const uint32_t s = (uint32_t)(it % p.stages);
         const uint32_t phase = (uint32_t)((it / p.stages) & 1);
-        const unsigned long long tile_idx = blockIdx.x + it * gridDim.x;
-        const unsigned long long t0 = tile_idx * p.tile;
+        const unsigned long long t0 = (gw + it * TW) * p.tile;
         const uint32_t nbytes = (uint32_t)tile_bytes(p, t0, end);
-        uint8_t *st = smem + p.off_stage + (size_t)s * p.stage_bytes;
+        uint8_t *st = stages + (size_t)s * p.stage_bytes;
 
-        if (BATCH && tid == 0) s_text0 = find_text(p.offsets, p.ntexts, t0);
-        bool ok = mbar_wait_bounded(&bars[s], phase);
-        ok = __syncthreads_and(ok);
+        const bool ok = __all_sync(0xffffffffu, mbar_wait_bounded(&bars[s], phase));
         if (!ok) {
-            if (tid == 0) {
+            if (lane == 0) {
                 record_error(PM_ERR_TIMEOUT);
-                // copies still in flight: tiles it .. it+stages-1
                 for (unsigned long long j = it; j < my_tiles && j < it + p.stages; ++j)
                     mbar_wait_bounded(&bars[j % p.stages], (uint32_t)((j / p.stages) & 1));
             }
@@ -267,247 +406,213 @@ __global__ void __launch_bounds__(512) pfac_scan_kernel(const KParams p)
         }
         const uint32_t nb16 = p.aligned ? (nbytes & ~15u) : 0u;
         if (nb16 < nbytes) {
-            for (uint32_t i = nb16 + tid; i < nbytes; i += T) st[i] = __ldg(p.text + t0 + i);
-            __syncthreads();
+            for (uint32_t i = nb16 + lane; i < nbytes; i += 32) st[i] = __ldg(p.text + t0 + i);
+            __syncwarp();
         }
 
         const uint32_t tile_n = (uint32_t)(total - t0 < p.tile ? total - t0 : p.tile);
-        unsigned long long text_end;
+        uint32_t cur = 0;
+        unsigned long long text_end = end;
         if (BATCH) {
-            cur = s_text0;
+            cur = find_text(p.offsets, p.ntexts, t0 + 4 * lane < total ? t0 + 4 * lane : t0);
             text_end = __ldg(p.offsets + cur + 1);
-        } else {
-            text_end = end;
         }
+        uint32_t rel_end = rel_end_of(text_end, t0);
+        uint32_t qn = 0;  // warp-uniform queue length
 
-        for (uint32_t li = 4 * tid; li < tile_n; li += 4 * T) {
-            uint32_t c[16];
-            {
-                const uint32_t *wp = reinterpret_cast<const uint32_t *>(st + li);
-#pragma unroll
-                for (int w = 0; w < 4; ++w) {
-                    if (w * 4 < KC + 4) {  // bytes li .. li+3+KC
-                        uint32_t word;
-                        if (MODE == MODE_CHECKED && li + 4 * w + 4 > p.stage_bytes) {
-                            record_error(PM_ERR_BOUNDS);
-                            word = 0;
-                        } else {
-                            word = wp[w];
-                        }
-#pragma unroll
-                        for (int b = 0; b < 4; ++b) c[4 * w + b] = (word >> (8 * b)) & 0xFFu;
-                    }
+        const uint32_t iters = (tile_n + 127) >> 7;
+        for (uint32_t i = 0; i < iters; ++i) {
+            const uint32_t lp0 = (i << 7) + 4 * lane;
+            const uint32_t *wp = reinterpret_cast<const uint32_t *>(st + lp0);
+            if (BATCH && lp0 < tile_n && t0 + lp0 >= text_end) {
+                while (t0 + lp0 >= text_end) {
+                    ++cur;
+                    text_end = __ldg(p.offsets + cur + 1);
                 }
-                if (!IDENT) {
-#pragma unroll
-                    for (int j = 0; j < KC + 4 && j < 16; ++j) c[j] = cls_of(c[j]);
-                }
+                rel_end = rel_end_of(text_end, t0);
             }
-            int32_t out[4];
+            uint32_t need = 0;  // bit q: position lp0+q must be walked
+            if (MODE != MODE_LOOKUPS && lp0 + 4 <= tile_n && lp0 + 4 + k <= rel_end) {
+                // Phase 1 fast path: four positions, all bytes up to
+                // lp0+3+k inside the text. The filter decides, in shared
+                // memory, which positions can reach depth k+1.
+                if (IDENT && KF >= 0) {
+                    const uint32_t w0 = wp[0];
+                    const uint32_t w1 = KF >= 1 ? wp[1] : 0u;
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                out[q] = -1;
-                const uint32_t lp = li + q;
-                if (lp >= tile_n) continue;
-                const unsigned long long pos = t0 + lp;
-                if (BATCH) {
-                    while (pos >= text_end) {
-                        if (acc) {
-                            atomicAdd(reinterpret_cast<unsigned long long *>(p.counts + cur), acc);
-                            acc = 0;
+                    for (int q = 0; q < 4; ++q) {
+                        const uint32_t x = q == 0 ? w0 : __funnelshift_r(w0, w1, 8 * q);
+                        const uint32_t idx = x & imask;
+                        const uint32_t word = idx >> 5;
+                        if (MODE == MODE_CHECKED && word >= p.filt_words) {
+                            record_error(PM_ERR_BOUNDS);
+                            continue;
                         }
-                        ++cur;
-                        text_end = __ldg(p.offsets + cur + 1);
+                        need |= ((s_filt[word] >> (idx & 31u)) & 1u) << q;
+                    }
+                } else {
+                    uint32_t c[16];
+#pragma unroll
+                    for (int w = 0; w < 4; ++w) {
+                        const uint32_t word = (uint32_t)(4 * w) < k + 4 ? wp[w] : 0u;
+#pragma unroll
+                        for (int b = 0; b < 4; ++b) c[4 * w + b] = class_of<IDENT>(s_lut, lane, (word >> (8 * b)) & 0xFFu);
+                    }
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        uint32_t code = 0, nc = 0;
+#pragma unroll
+                        for (int j = 0; j < 12; ++j) {
+                            if (j < (int)k) code = code * C + c[q + j];
+                            if (j == (int)k) nc = c[q + j];
+                        }
+                        if (k == 12) nc = c[q + 12];
+                        const uint32_t idx = (code << lw) | (nc & wmask);
+                        const uint32_t word = idx >> 5;
+                        if (MODE == MODE_CHECKED && word >= p.filt_words) {
+                            record_error(PM_ERR_BOUNDS);
+                            continue;
+                        }
+                        need |= ((s_filt[word] >> (idx & 31u)) & 1u) << q;
                     }
                 }
-                // walk limit inside the staged buffer
-                const unsigned long long lim64 = text_end - t0;
-                const uint32_t lim = lim64 < nbytes ? (uint32_t)lim64 : nbytes;
-
-                uint32_t v = 0, depth = 0;
-                bool walk = true;
-                if (MODE != MODE_LOOKUPS && pos + k <= text_end) {
-                    uint32_t code = 0;
-#pragma unroll
-                    for (int j = 0; j < KC; ++j)
-                        if (j < (int)k) code = IDENT ? (code << 8) | c[q + j] : code * C + c[q + j];
-                    uint32_t w = code >> 5, bit = code & 31u;
-                    if (MODE == MODE_CHECKED && w >= t.dense_words[k]) {
+            } else {
+                // ragged group: tile end, text boundary or too few bytes left
+                for (uint32_t q = 0; q < 4; ++q) {
+                    const uint32_t lp = lp0 + q;
+                    if (lp >= tile_n) break;
+                    const unsigned long long pos = t0 + lp;
+                    if (BATCH) {
+                        while (pos >= text_end) {
+                            ++cur;
+                            text_end = __ldg(p.offsets + cur + 1);
+                        }
+                        rel_end = rel_end_of(text_end, t0);
+                    }
+                    if (MODE == MODE_LOOKUPS || lp + k + 1 > rel_end) {
+                        need |= 1u << q;  // walked from the root in phase 2
+                        continue;
+                    }
+                    uint32_t idx;
+                    if (IDENT && KF >= 0) {
+                        uint32_t x = 0;
+                        for (uint32_t j = 0; j <= k; ++j) x |= (uint32_t)st[lp + j] << (8 * j);
+                        idx = x & imask;
+                    } else {
+                        uint32_t code = 0;
+                        for (uint32_t j = 0; j < k; ++j) code = code * C + class_of<IDENT>(s_lut, lane, st[lp + j]);
+                        idx = (code << lw) | (class_of<IDENT>(s_lut, lane, st[lp + k]) & wmask);
+                    }
+                    const uint32_t word = idx >> 5;
+                    if (MODE == MODE_CHECKED && word >= p.filt_words) {
                         record_error(PM_ERR_BOUNDS);
                         continue;
                     }
-                    const uint2 e = s_dense[w];
-                    if ((e.x >> bit) & 1u) {
-                        v = first_k + e.y + __popc(e.x & ((1u << bit) - 1u));
-                        depth = k;
-                        if (p.use_cm && pos + k < text_end) {
-                            uint32_t nc = 0;
-#pragma unroll
-                            for (int j = 1; j <= KC; ++j)
-                                if (j == (int)k) nc = c[q + j];
-                            if (MODE == MODE_CHECKED && v - first_k >= t.nlevel[k]) {
-                                record_error(PM_ERR_BOUNDS);
-                                continue;
-                            }
-                            if (!((s_cm[v - first_k] >> (nc & 31u)) & 1u)) walk = false;
-                        }
-                    } else {
-                        walk = false;  // stopped above depth k <= shortest pattern
-                    }
-                }
-                if (walk) {
-                    uint32_t lj = lp + depth;
-                    while (lj < lim) {
-                        const uint32_t b = st[lj];
-                        if (MODE == MODE_CHECKED && v >= t.n_nodes) {
-                            record_error(PM_ERR_BOUNDS);
-                            break;
-                        }
-                        const uint32_t r0 = __ldg(t.row_ptr + v), r1 = __ldg(t.row_ptr + v + 1);
-                        if (MODE == MODE_CHECKED && (r1 < r0 || r1 > t.nnz)) {
-                            record_error(PM_ERR_BOUNDS);
-                            break;
-                        }
-                        if (MODE == MODE_LOOKUPS) ++look;
-                        uint32_t e;
-                        bool found = false;
-                        if (p.binary) {
-                            uint32_t lo = r0, hi = r1;
-                            while (lo < hi) {
-                                uint32_t mid = (lo + hi) >> 1;
-                                if (__ldg(t.col + mid) < b) lo = mid + 1;
-                                else hi = mid;
-                            }
-                            e = lo;
-                            found = lo < r1 && __ldg(t.col + lo) == b;
-                        } else {
-                            for (e = r0; e < r1; ++e) {
-                                const uint32_t cb = __ldg(t.col + e);
-                                if (cb >= b) {
-                                    found = cb == b;
-                                    break;
-                                }
-                            }
-                        }
-                        if (!found) break;
-                        v = (uint32_t)__ldg(t.next + e);
-                        ++lj;
-                    }
-                    depth = lj - lp;
-                }
-                if (depth >= min_len) {
-                    const int2 em = __ldg(t.emit + v);
-                    out[q] = em.x;
-                    acc += (unsigned)em.y;
+                    need |= ((s_filt[word] >> (idx & 31u)) & 1u) << q;
                 }
             }
-            const unsigned long long pos0 = t0 + li;
-            if (p.ids_aligned && li + 3 < tile_n) {
-                __stcs(reinterpret_cast<int4 *>(p.ids + pos0), make_int4(out[0], out[1], out[2], out[3]));
+            // every position gets -1 now; phase 2 patches the matches
+            const unsigned long long pos0 = t0 + lp0;
+            if (p.ids_aligned && lp0 + 3 < tile_n) {
+                __stcs(reinterpret_cast<int4 *>(p.ids + pos0), make_int4(-1, -1, -1, -1));
             } else {
 #pragma unroll
                 for (int q = 0; q < 4; ++q)
-                    if (li + q < tile_n) __stcs(p.ids + pos0 + q, out[q]);
+                    if (lp0 + q < tile_n) __stcs(p.ids + pos0 + q, -1);
+            }
+            // warp ballot/popc compaction of the groups with work
+            const uint32_t mg = __ballot_sync(0xffffffffu, need != 0);
+            if (mg) {
+                const uint32_t tot = __popc(mg);
+                if (qn + tot > kQueue) {
+                    walk_queue<IDENT, BATCH, MODE>(p, queue, qn, st, t0, nbytes, end, k, s_lut,
+                                                   lane, acc, look);
+                    qn = 0;
+                }
+                if (need) queue[qn + __popc(mg & ((1u << lane) - 1u))] = lp0 | (need << 16);
+                qn += tot;
             }
         }
-        if (BATCH && acc) {
-            atomicAdd(reinterpret_cast<unsigned long long *>(p.counts + cur), acc);
-            acc = 0;
-        }
-        __syncthreads();  // stage s fully consumed
-        if (tid == 0 && it + p.stages < my_tiles) {
+        if (qn)
+            walk_queue<IDENT, BATCH, MODE>(p, queue, qn, st, t0, nbytes, end, k, s_lut, lane, acc,
+                                           look);
+
+        __syncwarp();  // stage s fully consumed by this warp
+        if (lane == 0 && it + p.stages < my_tiles) {
             fence_proxy_async();
-            issue_tile(p, smem, bars, s, blockIdx.x + (it + p.stages) * gridDim.x, end);
+            issue_tile(p, stages, bars, s, gw + (it + p.stages) * TW, end);
         }
     }
 
-    // CTA reductions: the single-text count, and lookups.
-    if (!BATCH || MODE == MODE_LOOKUPS) {
-        unsigned long long a = BATCH ? 0ull : acc;
-        unsigned long long l = look;
+    // warp reductions: single-text count and lookups
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            a += __shfl_xor_sync(0xffffffffu, a, o);
-            l += __shfl_xor_sync(0xffffffffu, l, o);
-        }
-        if (lane == 0) s_red[tid >> 5] = a;
-        __syncthreads();
-        if (tid < 32) {
-            unsigned long long x = tid < (T >> 5) ? s_red[tid] : 0ull;
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-            if (tid == 0 && x && !BATCH) atomicAdd(reinterpret_cast<unsigned long long *>(p.counts), x);
-        }
-        __syncthreads();
-        if (MODE == MODE_LOOKUPS) {
-            if (lane == 0) s_red[tid >> 5] = l;
-            __syncthreads();
-            if (tid < 32) {
-                unsigned long long x = tid < (T >> 5) ? s_red[tid] : 0ull;
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-                if (tid == 0 && x && p.lookups) atomicAdd(p.lookups, x);
-            }
-        }
+    for (int o = 16; o > 0; o >>= 1) {
+        acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        look += __shfl_xor_sync(0xffffffffu, look, o);
+    }
+    if (lane == 0) {
+        if (!BATCH && acc) atomicAdd(reinterpret_cast<unsigned long long *>(p.counts), acc);
+        if (MODE == MODE_LOOKUPS && look && p.lookups) atomicAdd(p.lookups, look);
     }
 }
 
 typedef void (*KernelFn)(KParams);
 
-template <int KC, bool IDENT>
+template <int KF, bool IDENT>
 KernelFn pick_mode(bool batch, int mode)
 {
     if (batch) {
         switch (mode) {
-        case MODE_CHECKED: return pfac_scan_kernel<KC, IDENT, true, MODE_CHECKED>;
-        case MODE_LOOKUPS: return pfac_scan_kernel<KC, IDENT, true, MODE_LOOKUPS>;
-        default: return pfac_scan_kernel<KC, IDENT, true, MODE_FAST>;
+        case MODE_CHECKED: return pfac_scan_kernel<KF, IDENT, true, MODE_CHECKED>;
+        case MODE_LOOKUPS: return pfac_scan_kernel<KF, IDENT, true, MODE_LOOKUPS>;
+        default: return pfac_scan_kernel<KF, IDENT, true, MODE_FAST>;
         }
     }
     switch (mode) {
-    case MODE_CHECKED: return pfac_scan_kernel<KC, IDENT, false, MODE_CHECKED>;
-    case MODE_LOOKUPS: return pfac_scan_kernel<KC, IDENT, false, MODE_LOOKUPS>;
-    default: return pfac_scan_kernel<KC, IDENT, false, MODE_FAST>;
+    case MODE_CHECKED: return pfac_scan_kernel<KF, IDENT, false, MODE_CHECKED>;
+    case MODE_LOOKUPS: return pfac_scan_kernel<KF, IDENT, false, MODE_LOOKUPS>;
+    default: return pfac_scan_kernel<KF, IDENT, false, MODE_FAST>;
     }
 }
 
+// Byte alphabet (C = 256): k is 0, 1 or 2 and fixed at compile time.
 KernelFn pick_kernel(uint32_t C, uint32_t k, bool batch, int mode)
 {
-    if (C == 256) return pick_mode<2, true>(batch, mode);  // k <= 2 at C = 256
-    if (k <= 4) return pick_mode<4, false>(batch, mode);
-    return pick_mode<12, false>(batch, mode);
+    if (C == 256) {
+        if (k == 0) return pick_mode<0, true>(batch, mode);
+        if (k == 1) return pick_mode<1, true>(batch, mode);
+        return pick_mode<2, true>(batch, mode);
+    }
+    return pick_mode<-1, false>(batch, mode);
 }
 
 uint32_t round16(uint64_t x) { return (uint32_t)((x + 15) & ~15ull); }
 
 struct Layout {
-    uint32_t off_cm, off_lut, off_bar, off_stage, stage_bytes, total;
-    uint32_t dense_u4, cm_u4, halo;
+    uint32_t off_lut, off_warp, warp_bytes, off_queue, off_stages, stage_bytes, total;
+    uint32_t filt_u4, filt_words, halo;
 };
 
+int width_index(int32_t bits) { return bits == 8 ? 0 : bits == 16 ? 1 : 2; }
+
+// Shared memory: [filter][class LUT] shared by the CTA, then one block per
+// warp: [mbarriers][walk queue][stages x (tile + halo)].
 Layout layout(const TrieDev &t, const pm_config &cfg)
 {
     Layout L{};
     const uint32_t k = (uint32_t)cfg.dense_k;
-    uint64_t dense_bytes = (uint64_t)t.dense_words[k] * 8;
-    L.dense_u4 = (uint32_t)(dense_bytes / 16);
-    uint32_t off = round16(dense_bytes);
-    L.off_cm = off;
-    if (cfg.childmask && t.childmask[k]) {
-        uint64_t cm_bytes = (uint64_t)((t.nlevel[k] + 3) / 4) * 16;
-        if (cm_bytes == 0) cm_bytes = 16;
-        L.cm_u4 = (uint32_t)(cm_bytes / 16);
-        off += (uint32_t)cm_bytes;
-    }
+    L.filt_words = t.filter_words[k][width_index(cfg.filter_bits)];
+    L.filt_u4 = L.filt_words / 4;
+    uint32_t off = round16((uint64_t)L.filt_words * 4);
     L.off_lut = off;
     if (t.C != 256) off += 64 * 32 * 4;
-    L.off_bar = off;
-    off += round16((uint64_t)kMaxStages * 8);
-    L.off_stage = off;
+    L.off_warp = off;
     L.halo = round16(t.max_len > 16 ? t.max_len : 16);
     L.stage_bytes = (uint32_t)cfg.tile + L.halo;
-    off += (uint32_t)cfg.stages * L.stage_bytes;
-    L.total = off;
+    L.off_queue = round16((uint64_t)kMaxStages * 8);
+    L.off_stages = L.off_queue + kQueue * 4;
+    L.warp_bytes = L.off_stages + (uint32_t)cfg.stages * L.stage_bytes;
+    L.total = off + (uint32_t)(cfg.threads / 32) * L.warp_bytes;
     return L;
 }
 
@@ -559,18 +664,22 @@ int launch_scan(const TrieDev &t, const pm_config &cfg, const ScanArgs &a, void 
     p.tile = (uint32_t)cfg.tile;
     p.halo = L.halo;
     p.k = (uint32_t)cfg.dense_k;
-    p.use_cm = (cfg.childmask && t.childmask[cfg.dense_k]) ? 1u : 0u;
+    p.lw = cfg.filter_bits == 8 ? 3u : cfg.filter_bits == 16 ? 4u : 5u;
+    p.filter = t.filter[cfg.dense_k][width_index(cfg.filter_bits)];
+    p.dense = cfg.dense_k > 0 ? t.dense[cfg.dense_k] : nullptr;
+    p.first_k = t.first[cfg.dense_k];
     p.binary = cfg.row_search ? 1u : 0u;
     p.stages = (uint32_t)cfg.stages;
     p.aligned = ((uintptr_t)a.text & 15u) == 0;
     p.ids_aligned = ((uintptr_t)a.ids & 15u) == 0;
-    p.off_cm = L.off_cm;
     p.off_lut = L.off_lut;
-    p.off_bar = L.off_bar;
-    p.off_stage = L.off_stage;
+    p.off_warp = L.off_warp;
+    p.warp_bytes = L.warp_bytes;
+    p.off_queue = L.off_queue;
+    p.off_stages = L.off_stages;
     p.stage_bytes = L.stage_bytes;
-    p.dense_u4 = L.dense_u4;
-    p.cm_u4 = L.cm_u4;
+    p.filt_u4 = L.filt_u4;
+    p.filt_words = L.filt_words;
 
     cudaError_t e;
     {
@@ -594,8 +703,10 @@ int launch_scan(const TrieDev &t, const pm_config &cfg, const ScanArgs &a, void 
     if (cfg.ctas_per_sm > 0 && cfg.ctas_per_sm < occ) occ = cfg.ctas_per_sm;
     unsigned long long grid = (unsigned long long)device_sms * occ;
     if (!batch) {
+        const unsigned long long warps = cfg.threads / 32;
         unsigned long long ntiles = (a.len + cfg.tile - 1) / cfg.tile;
-        if (ntiles < grid) grid = ntiles;
+        unsigned long long need = (ntiles + warps - 1) / warps;
+        if (need < grid) grid = need;
     }
     fn<<<(unsigned)grid, cfg.threads, L.total, st>>>(p);
     e = cudaGetLastError();

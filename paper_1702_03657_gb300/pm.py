@@ -63,7 +63,7 @@ class pm_trie_stats(C.Structure):
 
 class pm_config(C.Structure):
     _fields_ = [(f, C.c_int32) for f in (
-        "threads", "tile", "dense_k", "childmask", "row_search",
+        "threads", "tile", "dense_k", "filter_bits", "row_search",
         "ctas_per_sm", "stages", "checked")]
 
     def as_dict(self):

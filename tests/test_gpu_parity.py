@@ -69,7 +69,7 @@ def assert_same(ids, cnt, o_ids, o_cnt):
 
 def small_cfg(trie, **kw):
     c = pm.pm_get_config(trie)
-    c.update(threads=128, tile=1024, stages=2)
+    c.update(threads=128, tile=256, stages=2)
     c.update(kw)
     return c
 
@@ -110,26 +110,30 @@ def test_random_small_all_positions(seed, alphabet, npat, lo, hi, n):
 
 def test_config_sweep():
     """Every launch configuration gives the same bits."""
-    wl = W.random_case(11, 400, 40_000 + 77, 4, 3, 14, plant_rate=0.05)
-    t = pm.pm_build(wl.patterns)
-    st = pm.pm_stats(t)
-    o_ids, o_cnt, _ = oracle.Trie(wl.patterns).scan(wl.text)
-    base = pm.pm_get_config(t)
-    for threads in (128, 256, 512):
-        for tile in (4 * threads, 8192):
-            for k in sorted({1, 2, st["dense_k_max"]}):
-                for cm in (0, 1):
-                    for rs in (0, 1):
-                        for stages in (2, 4):
+    for wl in (W.random_case(11, 400, 40_000 + 77, 4, 3, 14, plant_rate=0.05),
+               W.paper_scale(3, text_bytes=300_000 + 9, n_patterns=3000)):
+        t = pm.pm_build(wl.patterns)
+        st = pm.pm_stats(t)
+        o_ids, o_cnt, _ = oracle.Trie(wl.patterns).scan(wl.text)
+        base = pm.pm_get_config(t)
+        tried = 0
+        for threads in (128, 256, 1024):
+            for tile in (128, 1024, 8192):
+                for k in sorted({0, 1, st["dense_k_max"]}):
+                    for bits in (8, 16, 32):
+                        for rs in (0, 1):
                             c = dict(base, threads=threads, tile=tile, dense_k=k,
-                                     childmask=cm, row_search=rs, stages=stages,
+                                     filter_bits=bits, row_search=rs,
+                                     stages=2 + (tile == 128) * 2,
                                      checked=int(threads == 256))
                             try:
                                 pm.pm_set_config(t, c)
                             except pm.PMError:
-                                continue  # e.g. no child filter at this k
+                                continue  # e.g. no filter of that width at this k
                             ids, cnt, _ = gpu_scan(t, wl.text, cfg=c)
                             assert_same(ids, cnt, o_ids, o_cnt)
+                            tried += 1
+        assert tried >= 20
     assert pm.pm_device_error() == 0
 
 
