@@ -70,33 +70,33 @@ int32_t pick_bits(const pm_trie *h, int32_t k)
     return 0;
 }
 
-// Default launch configuration: 32 independent warps per CTA with 2 KiB
-// warp tiles double-buffered and the deepest filter level; shrunk until it
-// fits the SM.
+// Default launch configuration: as many independent warps as fit (up to 32
+// per CTA, one CTA per SM) with 1-2 KiB warp tiles double-buffered, at the
+// deepest filter level that fits; an autotuner may refine it.
 pm_config default_config(const pm_trie *h, int smem_limit)
 {
     pm_config c{};
-    c.threads = 1024;
-    c.tile = 2048;
-    c.dense_k = (int32_t)h->host.dense_k_max;
-    c.filter_bits = pick_bits(h, c.dense_k);
     c.row_search = 0;
     c.ctas_per_sm = 0;
     c.stages = 2;
     c.checked = 0;
     const uint64_t limit = (uint64_t)smem_limit - 1024;
-    while (pm::scan_smem_bytes(h->dev, c) > limit) {
-        if (c.threads > 512) c.threads /= 2;
-        else if (c.tile > 1024) c.tile /= 2;
-        else if (c.dense_k > 0) {
-            --c.dense_k;
-            c.filter_bits = pick_bits(h, c.dense_k);
-            c.threads = 1024;
-            c.tile = 2048;
-        } else if (c.threads > 128) c.threads /= 2;
-        else if (c.tile > 128) c.tile /= 2;
-        else break;
+    for (int32_t k = (int32_t)h->host.dense_k_max; k >= 0; --k) {
+        c.dense_k = k;
+        c.filter_bits = pick_bits(h, k);
+        if (!c.filter_bits) continue;
+        for (int32_t threads : {1024, 512, 256, 128}) {
+            for (int32_t tile : {2048, 1536, 1024, 512, 256, 128}) {
+                c.threads = threads;
+                c.tile = tile;
+                if (pm::scan_smem_bytes(h->dev, c) <= limit) return c;
+            }
+        }
     }
+    c.dense_k = 0;
+    c.filter_bits = 8;
+    c.threads = 128;
+    c.tile = 128;
     return c;
 }
 

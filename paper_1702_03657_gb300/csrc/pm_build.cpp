@@ -198,7 +198,7 @@ int build_host_trie(const uint8_t *const *patterns, const uint32_t *lengths,
     const bool le = t.C == 256;
     std::vector<uint64_t> code(nn, 0), fcode(nn, 0);
     for (uint32_t v = 0; v < nn; ++v) {
-        if (t.depth[v] >= K) continue;
+        if (t.depth[v] > K) break;  // BFS: depths never decrease
         for (uint32_t e = t.row_ptr[v]; e < t.row_ptr[v + 1]; ++e) {
             code[t.next[e]] = code[v] * t.C + t.cls[t.col[e]];
             fcode[t.next[e]] = le ? fcode[v] | ((uint64_t)t.col[e] << (8 * t.depth[v]))
@@ -208,7 +208,7 @@ int build_host_trie(const uint8_t *const *patterns, const uint32_t *lengths,
     std::vector<uint32_t> lvl_begin(K + 2, nn), lvl_count(K + 2, 0);
     for (uint32_t v = 0; v < nn; ++v) {
         uint32_t d = t.depth[v];
-        if (d > K) break;  // BFS: depths never decrease
+        if (d > K + 1) break;
         if (lvl_count[d]++ == 0) lvl_begin[d] = v;
     }
     for (uint32_t k = 0; k <= K; ++k) {
@@ -244,6 +244,16 @@ int build_host_trie(const uint8_t *const *patterns, const uint32_t *lengths,
             words = (words + 3) & ~3ull;  // 16-byte units
             std::vector<uint32_t> &f = t.filter[k][wi];
             f.assign(words, 0);
+            if (le && k >= kBloomK) {
+                // byte alphabet, k >= 2: blocked Bloom filter of the paths of
+                // length k+1 (read little-endian) over 2^(8k + log2 W) bits
+                const uint32_t word_bits = 8 * k + (3 + wi) - 5;
+                for (uint32_t i = 0; i < lvl_count[k + 1]; ++i) {
+                    const BloomProbe b = bloom_probe((uint32_t)fcode[lvl_begin[k + 1] + i], word_bits);
+                    f[b.word] |= b.mask;
+                }
+                continue;
+            }
             for (uint32_t i = 0; i < lvl_count[k]; ++i) {
                 const uint32_t v = lvl_begin[k] + i;
                 const uint64_t c = fcode[v];

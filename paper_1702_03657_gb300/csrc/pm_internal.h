@@ -6,6 +6,7 @@
 #include <string>
 #include <vector>
 
+#include <cuda_runtime.h>
 #include <vector_types.h>
 
 #include "pm.h"
@@ -42,6 +43,25 @@ constexpr int kFilterWidths = 3;
 // because BFS numbers the depth-k nodes contiguously in code order. Stored
 // as uint2 {bits, base} per 32 codes.
 //
+// Byte alphabet with k >= kBloomK: the filter is instead a blocked Bloom
+// filter over 2^(8k + log2 W) bits of the paths of length k+1, each read as
+// the little-endian integer x = sum_j b_j << 8j. One multiplicative hash
+// h = hi32((x << 8) * M) picks a 32-bit word (its top bits) and two bits in
+// it (its low 10 bits); both are set for every such path. A clear bit
+// proves that the (k+1)-gram is not a root path. The depth-k node is then
+// looked up in the dense table, which also tells whether the k-gram itself
+// is a path.
+constexpr uint32_t kBloomK = 2;
+constexpr uint32_t kBloomMul = 0x9E3779B1u;  // Knuth's golden-ratio multiplier
+struct BloomProbe {
+    uint32_t word, mask;
+};
+__host__ __device__ inline BloomProbe bloom_probe(uint32_t x, uint32_t word_bits)
+{
+    const uint32_t h = (uint32_t)(((uint64_t)(x << 8) * kBloomMul) >> 32);
+    return {h >> (32u - word_bits), (1u << (h & 31u)) | (1u << ((h >> 5) & 31u))};
+}
+
 // Filter of level k and width W (shared memory): a bitset of C^k * W bits.
 // For a k-gram spelling a root path and a next class c_k, the bit
 //   code*W + (c_k mod W)                         (C < 256), or

@@ -41,6 +41,7 @@ __device__ int g_pm_dev_error;
 namespace {
 
 constexpr long long kWaitBudget = 4000000000LL;  // SM clocks (~2 s)
+constexpr uint32_t kSuspendHintNs = 1000000u;      // 1 ms per try_wait
 constexpr int kMaxStages = 4;
 
 enum Mode { MODE_FAST = 0, MODE_CHECKED = 1, MODE_LOOKUPS = 2 };
@@ -56,7 +57,7 @@ struct KParams {
     int64_t *counts;
     unsigned long long *lookups;
     const uint32_t *filter;     // filter table of level k, width W (global)
-    const uint2 *dense;         // dense table of level k (k >= 1)
+    const uint2 *dense;         // dense table of level k (k >= 1, global)
     uint32_t first_k;           // BFS id of the first depth-k node
     uint32_t tile;
     uint32_t halo;
@@ -67,11 +68,11 @@ struct KParams {
     uint32_t aligned;
     uint32_t ids_aligned;
     // shared-memory layout (byte offsets)
-    uint32_t off_lut, off_warp;   // shared tables, then per-warp blocks
+    uint32_t off_dense, off_lut, off_warp;  // shared tables, then per-warp blocks
     uint32_t warp_bytes;          // bytes of one warp's block
     uint32_t off_queue, off_stages;  // inside a warp's block (after its mbarriers)
     uint32_t stage_bytes;         // tile + halo
-    uint32_t filt_u4;             // filter size in 16-byte units
+    uint32_t filt_u4, dense_u4;   // table sizes in 16-byte units
     uint32_t filt_words;          // filter size in u32 words
 };
 
@@ -98,15 +99,17 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *bar)
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
+// One try_wait: the thread is suspended until the phase completes or the
+// hinted time (ns) passes, so a waiting warp takes no issue slots.
 __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t phase)
 {
     uint32_t done;
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
         "selp.u32 %0, 1, 0, p;\n\t}"
         : "=r"(done)
-        : "r"(smem_u32(bar)), "r"(phase)
+        : "r"(smem_u32(bar)), "r"(phase), "r"(kSuspendHintNs)
         : "memory");
     return done != 0;
 }
@@ -146,6 +149,29 @@ __device__ __forceinline__ void record_error(int code)
     atomicCAS(&g_pm_dev_error, 0, code);
 }
 
+// L2 policy "evict last" for the trie: it stays resident while the text
+// and the ids stream through L2.
+__device__ __forceinline__ uint64_t policy_evict_last()
+{
+    uint64_t pol;
+    asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
+
+__device__ __forceinline__ uint32_t ld_trie_u32(const void *ptr, uint64_t pol)
+{
+    uint32_t v;
+    asm volatile("ld.global.nc.L2::cache_hint.u32 %0, [%1], %2;" : "=r"(v) : "l"(ptr), "l"(pol));
+    return v;
+}
+
+__device__ __forceinline__ uint32_t ld_trie_u8(const void *ptr, uint64_t pol)
+{
+    uint32_t v;
+    asm volatile("ld.global.nc.L2::cache_hint.u8 %0, [%1], %2;" : "=r"(v) : "l"(ptr), "l"(pol));
+    return v;
+}
+
 // Bytes staged for the tile at t0: tile + halo, clipped to the readable end
 // (the total in batch mode, the single text's limit otherwise).
 __device__ __forceinline__ unsigned long long tile_bytes(const KParams &p, unsigned long long t0,
@@ -156,12 +182,12 @@ __device__ __forceinline__ unsigned long long tile_bytes(const KParams &p, unsig
     return left < want ? left : want;
 }
 
-// Issue the TMA copy of tile `tile_idx` into stage `s` of a warp (lane 0).
+// Issue the TMA copy of the tile at text offset t0 into stage `s` of a warp
+// (lane 0).
 __device__ __forceinline__ void issue_tile(const KParams &p, uint8_t *stages, uint64_t *bars,
-                                           uint32_t s, unsigned long long tile_idx,
+                                           uint32_t s, unsigned long long t0,
                                            unsigned long long end)
 {
-    unsigned long long t0 = tile_idx * p.tile;
     uint32_t nb = (uint32_t)tile_bytes(p, t0, end);
     uint32_t nb16 = nb & ~15u;
     if (p.aligned && nb16) {
@@ -186,36 +212,42 @@ __device__ __forceinline__ uint32_t find_text(const uint64_t *off, uint32_t ntex
     return lo;
 }
 
-// Per-warp walk queue: one u32 entry per 4-position group that has at least
-// one position to walk: tile-relative position of the group | mask << 16.
-constexpr int kQueue = 128;  // >= the 32 groups of one warp step
+// Per-warp walk queue of 4-position groups. Entry x = tile-relative position
+// of the group | positions to walk << 16 | of those, positions walked from
+// the root << 20; y = the warp's tile sequence number. Walks read the text
+// from global memory, so queued groups outlive their tile's staging buffer
+// and are walked in rounds of at least one group per lane.
+constexpr uint32_t kQueue = 64;    // >= 31 pending + 32 from one warp step
+constexpr uint32_t kRound = 32;    // groups that trigger a round
 
-// Walk the CRS rows from node v at staged byte lj until the first mismatch
-// or lj == lim (Section II-C). Returns the deepest node; lj is advanced.
+// Walk the CRS rows from node v with the text byte at j until the first
+// mismatch or the text end (Section II-C). The byte and the row bounds are
+// fetched together; the first column entry and its next state too. Returns
+// the deepest node; j is advanced past the matched bytes.
 template <int MODE>
-__device__ __forceinline__ uint32_t crs_walk(const TrieDev &t, const uint8_t *st, uint32_t &lj,
-                                             uint32_t lim, uint32_t v, uint32_t binary,
-                                             unsigned long long &look)
+__device__ __forceinline__ uint32_t crs_walk(const TrieDev &t, const uint8_t *text,
+                                             unsigned long long &j, unsigned long long tend,
+                                             uint32_t v, uint32_t binary, unsigned long long &look)
 {
-    while (lj < lim) {
-        const uint32_t b = st[lj];
+    const uint64_t pol = policy_evict_last();
+    while (j < tend) {
         if (MODE == MODE_CHECKED && v >= t.n_nodes) {
             record_error(PM_ERR_BOUNDS);
             break;
         }
-        const uint32_t r0 = __ldg(t.row_ptr + v), r1 = __ldg(t.row_ptr + v + 1);
+        const uint32_t b = __ldg(text + j);
+        const uint32_t r0 = ld_trie_u32(t.row_ptr + v, pol), r1 = ld_trie_u32(t.row_ptr + v + 1, pol);
         if (MODE == MODE_CHECKED && (r1 < r0 || r1 > t.nnz)) {
             record_error(PM_ERR_BOUNDS);
             break;
         }
         if (MODE == MODE_LOOKUPS) ++look;
         if (r1 == r0) break;  // leaf
-        // the first column entry and its next state are fetched together
-        const uint32_t c0 = __ldg(t.col + r0);
-        const uint32_t n0 = (uint32_t)__ldg(t.next + r0);
+        const uint32_t c0 = ld_trie_u8(t.col + r0, pol);
+        const uint32_t n0 = ld_trie_u32(t.next + r0, pol);
         if (c0 == b) {
             v = n0;
-            ++lj;
+            ++j;
             continue;
         }
         if (c0 > b || r1 - r0 == 1) break;
@@ -225,14 +257,14 @@ __device__ __forceinline__ uint32_t crs_walk(const TrieDev &t, const uint8_t *st
             uint32_t lo = r0 + 1, hi = r1;
             while (lo < hi) {
                 const uint32_t mid = (lo + hi) >> 1;
-                if (__ldg(t.col + mid) < b) lo = mid + 1;
+                if (ld_trie_u8(t.col + mid, pol) < b) lo = mid + 1;
                 else hi = mid;
             }
             e = lo;
-            found = lo < r1 && __ldg(t.col + lo) == b;
+            found = lo < r1 && ld_trie_u8(t.col + lo, pol) == b;
         } else {
             for (e = r0 + 1; e < r1; ++e) {
-                const uint32_t cb = __ldg(t.col + e);
+                const uint32_t cb = ld_trie_u8(t.col + e, pol);
                 if (cb >= b) {
                     found = cb == b;
                     break;
@@ -240,8 +272,8 @@ __device__ __forceinline__ uint32_t crs_walk(const TrieDev &t, const uint8_t *st
             }
         }
         if (!found) break;
-        v = (uint32_t)__ldg(t.next + e);
-        ++lj;
+        v = ld_trie_u32(t.next + e, pol);
+        ++j;
     }
     return v;
 }
@@ -261,53 +293,55 @@ __device__ __forceinline__ uint32_t class_of(const uint32_t *s_lut, uint32_t lan
     return (s_lut[(b >> 2) * 32 + lane] >> ((b & 3) * 8)) & 0xFFu;
 }
 
-// Phase 2: every lane takes queued groups and walks their flagged positions
-// from the depth-k node (found with the dense table; the filter proved the
-// k-gram is a root path) or, near a text end, from the root. Positions whose
-// walk finds a match get their id patched and their count added.
+// Phase 2: every lane takes queued groups and walks their flagged positions,
+// each from its depth-k node (k-gram code from the text, node from the dense
+// table; a k-gram that is not a root path stops the walk above depth k,
+// without a match) or from the root. A walk that finds a match patches its
+// position's id and adds its count.
 template <bool IDENT, bool BATCH, int MODE>
-__device__ __forceinline__ void walk_queue(const KParams &p, const uint32_t *queue, uint32_t qn,
-                                           const uint8_t *st, unsigned long long t0,
-                                           uint32_t nbytes, unsigned long long end, uint32_t k,
+__device__ __forceinline__ void walk_queue(const KParams &p, const uint2 *queue, uint32_t qn,
+                                           unsigned long long gw, unsigned long long TW,
+                                           unsigned long long end, uint32_t k,
                                            const uint32_t *s_lut, uint32_t lane,
                                            unsigned long long &acc, unsigned long long &look)
 {
     const TrieDev &t = p.t;
     __syncwarp();
-    for (uint32_t j = lane; j < qn; j += 32) {
-        const uint32_t e = queue[j];
-        const uint32_t g0 = e & 0xFFFFu;
-        uint32_t m = e >> 16;
-        uint32_t txt = 0;
+    for (uint32_t i = lane; i < qn; i += 32) {
+        const uint2 e = queue[i];
+        const unsigned long long g0 = (gw + e.y * TW) * p.tile + (e.x & 0xFFFFu);
+        uint32_t m = (e.x >> 16) & 0xFu;
+        const uint32_t rootm = e.x >> 20;
         unsigned long long tend = end;
+        uint32_t txt = 0;
         if (BATCH) {
-            txt = find_text(p.offsets, p.ntexts, t0 + g0 + (__ffs(m) - 1));
+            txt = find_text(p.offsets, p.ntexts, g0 + (__ffs(m) - 1));
             tend = __ldg(p.offsets + txt + 1);
         }
         while (m) {
             const uint32_t q = __ffs(m) - 1;
             m &= m - 1;
-            const uint32_t lp = g0 + q;
-            const unsigned long long pos = t0 + lp;
+            const unsigned long long pos = g0 + q;
             if (BATCH) {
                 while (pos >= tend) {
                     ++txt;
                     tend = __ldg(p.offsets + txt + 1);
                 }
             }
-            const unsigned long long lim64 = tend - t0;
-            const uint32_t lim = lim64 < nbytes ? (uint32_t)lim64 : nbytes;
-            uint32_t v = 0, lj = lp;
-            if (MODE != MODE_LOOKUPS && k > 0 && pos + k < tend) {
+            uint32_t v = 0;
+            unsigned long long j = pos;
+            if (!((rootm >> q) & 1u) && k > 0) {
                 uint32_t code = 0;
                 for (uint32_t j2 = 0; j2 < k; ++j2)
-                    code = code * t.C + class_of<IDENT>(s_lut, lane, st[lp + j2]);
+                    code = code * t.C + class_of<IDENT>(s_lut, lane, __ldg(p.text + pos + j2));
                 const uint2 d = __ldg(p.dense + (code >> 5));
-                v = p.first_k + d.y + __popc(d.x & ((1u << (code & 31u)) - 1u));
-                lj = lp + k;
+                const uint32_t bit = code & 31u;
+                if (!((d.x >> bit) & 1u)) continue;
+                v = p.first_k + d.y + __popc(d.x & ((1u << bit) - 1u));
+                j = pos + k;
             }
-            v = crs_walk<MODE>(t, st, lj, lim, v, p.binary, look);
-            if (lj - lp >= t.min_len) {
+            v = crs_walk<MODE>(t, p.text, j, tend, v, p.binary, look);
+            if (j - pos >= t.min_len) {
                 const int2 em = __ldg(t.emit + v);
                 if (em.y) {
                     p.ids[pos] = em.x;
@@ -366,32 +400,33 @@ __global__ void __launch_bounds__(1024, 1) pfac_scan_kernel(const KParams p)
 
     uint8_t *wsm = smem + p.off_warp + (size_t)warp * p.warp_bytes;
     uint64_t *bars = reinterpret_cast<uint64_t *>(wsm);
-    uint32_t *queue = reinterpret_cast<uint32_t *>(wsm + p.off_queue);
+    uint2 *queue = reinterpret_cast<uint2 *>(wsm + p.off_queue);
     uint8_t *stages = wsm + p.off_stages;
 
+    const unsigned long long tstride = TW * p.tile;  // text between a warp's tiles
     if (lane == 0) {
         for (uint32_t s = 0; s < p.stages; ++s) mbar_init(&bars[s], 1);
         fence_mbar_init();
         const unsigned long long pre = my_tiles < p.stages ? my_tiles : p.stages;
         for (unsigned long long i = 0; i < pre; ++i)
-            issue_tile(p, stages, bars, (uint32_t)i, gw + i * TW, end);
+            issue_tile(p, stages, bars, (uint32_t)i, (gw + i * TW) * p.tile, end);
     }
     __syncwarp();
 
     const uint32_t k = KF >= 0 ? (uint32_t)KF : p.k;
     const uint32_t C = t.C;
-    const uint32_t min_len = t.min_len;
     const uint32_t lw = p.lw;
     const uint32_t wmask = (1u << lw) - 1u;
     // IDENT: filter bit index = low 8k+lw bits of the little-endian window
     const uint32_t imask = KF >= 0 ? (uint32_t)((1ull << (8 * (KF >= 0 ? KF : 0) + lw)) - 1ull) : 0u;
     unsigned long long acc = 0;   // matches (single text)
     unsigned long long look = 0;  // lookups (MODE_LOOKUPS)
+    uint32_t qn = 0;              // warp-uniform queue length
 
-    for (unsigned long long it = 0; it < my_tiles; ++it) {
-        const uint32_t s = (uint32_t)(it % p.stages);
-        const uint32_t phase = (uint32_t)((it / p.stages) & 1);
-        const unsigned long long t0 = (gw + it * TW) * p.tile;
+    uint32_t s = 0, phase = 0;            // stage and its mbarrier phase
+    unsigned long long t0 = gw * p.tile;  // start of the current tile
+    const unsigned long long ahead = (unsigned long long)p.stages * tstride;
+    for (unsigned long long it = 0; it < my_tiles; ++it, t0 += tstride) {
         const uint32_t nbytes = (uint32_t)tile_bytes(p, t0, end);
         uint8_t *st = stages + (size_t)s * p.stage_bytes;
 
@@ -399,8 +434,11 @@ __global__ void __launch_bounds__(1024, 1) pfac_scan_kernel(const KParams p)
         if (!ok) {
             if (lane == 0) {
                 record_error(PM_ERR_TIMEOUT);
-                for (unsigned long long j = it; j < my_tiles && j < it + p.stages; ++j)
-                    mbar_wait_bounded(&bars[j % p.stages], (uint32_t)((j / p.stages) & 1));
+                // copies still in flight: tiles it .. it+stages-1
+                for (unsigned long long j = 0; j < p.stages && it + j < my_tiles; ++j) {
+                    const uint32_t sj = (uint32_t)((s + j) % p.stages);
+                    mbar_wait_bounded(&bars[sj], phase ^ (uint32_t)((s + j) >= p.stages));
+                }
             }
             return;
         }
@@ -418,7 +456,13 @@ __global__ void __launch_bounds__(1024, 1) pfac_scan_kernel(const KParams p)
             text_end = __ldg(p.offsets + cur + 1);
         }
         uint32_t rel_end = rel_end_of(text_end, t0);
-        uint32_t qn = 0;  // warp-uniform queue length
+        // groups [lp0, lp0+4) with lp0 + 4 <= fast_n take the fast path
+        auto fast_bound = [&]() -> uint32_t {
+            const uint32_t r = rel_end >= k ? rel_end - k : 0u;
+            return r < tile_n ? r : tile_n;
+        };
+        uint32_t fast_n = fast_bound();
+        int32_t *idt = p.ids + t0;  // this tile's ids
 
         const uint32_t iters = (tile_n + 127) >> 7;
         for (uint32_t i = 0; i < iters; ++i) {
@@ -430,13 +474,33 @@ __global__ void __launch_bounds__(1024, 1) pfac_scan_kernel(const KParams p)
                     text_end = __ldg(p.offsets + cur + 1);
                 }
                 rel_end = rel_end_of(text_end, t0);
+                fast_n = fast_bound();
             }
-            uint32_t need = 0;  // bit q: position lp0+q must be walked
-            if (MODE != MODE_LOOKUPS && lp0 + 4 <= tile_n && lp0 + 4 + k <= rel_end) {
+            uint32_t need = 0;   // bit q: position lp0+q passed the filter
+            uint32_t rootm = 0;  // bit q: position lp0+q is walked from the root
+            if (MODE != MODE_LOOKUPS && lp0 + 4 <= fast_n) {
                 // Phase 1 fast path: four positions, all bytes up to
                 // lp0+3+k inside the text. The filter decides, in shared
                 // memory, which positions can reach depth k+1.
-                if (IDENT && KF >= 0) {
+                if (IDENT && KF >= (int)kBloomK) {
+                    // blocked Bloom test of the (k+1)-gram at each position
+                    const uint32_t w0 = wp[0], w1 = wp[1];
+                    const uint32_t sh = 32u - (8u * KF + lw - 5u);
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const uint32_t win = q == 0 ? w0 : __funnelshift_r(w0, w1, 8 * q);
+                        // bytes q .. q+k, shifted to the top (x << 8)
+                        const uint32_t x8 = win << (24 - 8 * KF);
+                        const uint32_t h = __umulhi(x8, kBloomMul);
+                        const uint32_t word = h >> sh;
+                        const uint32_t mask = (1u << (h & 31u)) | (1u << ((h >> 5) & 31u));
+                        if (MODE == MODE_CHECKED && word >= p.filt_words) {
+                            record_error(PM_ERR_BOUNDS);
+                            continue;
+                        }
+                        need |= (uint32_t)((s_filt[word] & mask) == mask) << q;
+                    }
+                } else if (IDENT && KF >= 0) {
                     const uint32_t w0 = wp[0];
                     const uint32_t w1 = KF >= 1 ? wp[1] : 0u;
 #pragma unroll
@@ -456,18 +520,19 @@ __global__ void __launch_bounds__(1024, 1) pfac_scan_kernel(const KParams p)
                     for (int w = 0; w < 4; ++w) {
                         const uint32_t word = (uint32_t)(4 * w) < k + 4 ? wp[w] : 0u;
 #pragma unroll
-                        for (int b = 0; b < 4; ++b) c[4 * w + b] = class_of<IDENT>(s_lut, lane, (word >> (8 * b)) & 0xFFu);
+                        for (int b = 0; b < 4; ++b)
+                            c[4 * w + b] = class_of<IDENT>(s_lut, lane, (word >> (8 * b)) & 0xFFu);
                     }
 #pragma unroll
                     for (int q = 0; q < 4; ++q) {
-                        uint32_t code = 0, nc = 0;
+                        uint32_t cd = 0, nc = 0;
 #pragma unroll
                         for (int j = 0; j < 12; ++j) {
-                            if (j < (int)k) code = code * C + c[q + j];
+                            if (j < (int)k) cd = cd * C + c[q + j];
                             if (j == (int)k) nc = c[q + j];
                         }
                         if (k == 12) nc = c[q + 12];
-                        const uint32_t idx = (code << lw) | (nc & wmask);
+                        const uint32_t idx = (cd << lw) | (nc & wmask);
                         const uint32_t word = idx >> 5;
                         if (MODE == MODE_CHECKED && word >= p.filt_words) {
                             record_error(PM_ERR_BOUNDS);
@@ -477,7 +542,9 @@ __global__ void __launch_bounds__(1024, 1) pfac_scan_kernel(const KParams p)
                     }
                 }
             } else {
-                // ragged group: tile end, text boundary or too few bytes left
+                // ragged group (tile end, text boundary, last k bytes of a
+                // text): every position that passes the filter, or that is
+                // too close to its text end to test, is walked from the root
                 for (uint32_t q = 0; q < 4; ++q) {
                     const uint32_t lp = lp0 + q;
                     if (lp >= tile_n) break;
@@ -488,61 +555,74 @@ __global__ void __launch_bounds__(1024, 1) pfac_scan_kernel(const KParams p)
                             text_end = __ldg(p.offsets + cur + 1);
                         }
                         rel_end = rel_end_of(text_end, t0);
+                        fast_n = fast_bound();
                     }
                     if (MODE == MODE_LOOKUPS || lp + k + 1 > rel_end) {
-                        need |= 1u << q;  // walked from the root in phase 2
+                        rootm |= 1u << q;
                         continue;
                     }
-                    uint32_t idx;
-                    if (IDENT && KF >= 0) {
+                    uint32_t word, bits;
+                    if (IDENT && KF >= (int)kBloomK) {
                         uint32_t x = 0;
                         for (uint32_t j = 0; j <= k; ++j) x |= (uint32_t)st[lp + j] << (8 * j);
-                        idx = x & imask;
+                        const BloomProbe b = bloom_probe(x, 8u * KF + lw - 5u);
+                        word = b.word;
+                        bits = b.mask;
+                    } else if (IDENT && KF >= 0) {
+                        uint32_t x = 0;
+                        for (uint32_t j = 0; j <= k; ++j) x |= (uint32_t)st[lp + j] << (8 * j);
+                        const uint32_t idx = x & imask;
+                        word = idx >> 5;
+                        bits = 1u << (idx & 31u);
                     } else {
-                        uint32_t code = 0;
-                        for (uint32_t j = 0; j < k; ++j) code = code * C + class_of<IDENT>(s_lut, lane, st[lp + j]);
-                        idx = (code << lw) | (class_of<IDENT>(s_lut, lane, st[lp + k]) & wmask);
+                        uint32_t cd = 0;
+                        for (uint32_t j = 0; j < k; ++j) cd = cd * C + class_of<IDENT>(s_lut, lane, st[lp + j]);
+                        const uint32_t idx = (cd << lw) | (class_of<IDENT>(s_lut, lane, st[lp + k]) & wmask);
+                        word = idx >> 5;
+                        bits = 1u << (idx & 31u);
                     }
-                    const uint32_t word = idx >> 5;
                     if (MODE == MODE_CHECKED && word >= p.filt_words) {
                         record_error(PM_ERR_BOUNDS);
                         continue;
                     }
-                    need |= ((s_filt[word] >> (idx & 31u)) & 1u) << q;
+                    if ((s_filt[word] & bits) == bits) rootm |= 1u << q;
                 }
             }
             // every position gets -1 now; phase 2 patches the matches
-            const unsigned long long pos0 = t0 + lp0;
-            if (p.ids_aligned && lp0 + 3 < tile_n) {
-                __stcs(reinterpret_cast<int4 *>(p.ids + pos0), make_int4(-1, -1, -1, -1));
+            if (p.ids_aligned && lp0 + 4 <= tile_n) {
+                __stcs(reinterpret_cast<int4 *>(idt + lp0), make_int4(-1, -1, -1, -1));
             } else {
 #pragma unroll
                 for (int q = 0; q < 4; ++q)
-                    if (lp0 + q < tile_n) __stcs(p.ids + pos0 + q, -1);
+                    if (lp0 + q < tile_n) __stcs(idt + lp0 + q, -1);
             }
             // warp ballot/popc compaction of the groups with work
-            const uint32_t mg = __ballot_sync(0xffffffffu, need != 0);
+            const uint32_t work = need | rootm;
+            const uint32_t mg = __ballot_sync(0xffffffffu, work != 0);
             if (mg) {
-                const uint32_t tot = __popc(mg);
-                if (qn + tot > kQueue) {
-                    walk_queue<IDENT, BATCH, MODE>(p, queue, qn, st, t0, nbytes, end, k, s_lut,
-                                                   lane, acc, look);
+                if (work)
+                    queue[qn + __popc(mg & ((1u << lane) - 1u))] =
+                        make_uint2(lp0 | (work << 16) | (rootm << 20), (uint32_t)it);
+                qn += __popc(mg);
+                if (qn >= kRound) {
+                    walk_queue<IDENT, BATCH, MODE>(p, queue, qn, gw, TW, end, k, s_lut, lane, acc,
+                                                   look);
                     qn = 0;
                 }
-                if (need) queue[qn + __popc(mg & ((1u << lane) - 1u))] = lp0 | (need << 16);
-                qn += tot;
             }
         }
-        if (qn)
-            walk_queue<IDENT, BATCH, MODE>(p, queue, qn, st, t0, nbytes, end, k, s_lut, lane, acc,
-                                           look);
 
         __syncwarp();  // stage s fully consumed by this warp
         if (lane == 0 && it + p.stages < my_tiles) {
             fence_proxy_async();
-            issue_tile(p, stages, bars, s, gw + (it + p.stages) * TW, end);
+            issue_tile(p, stages, bars, s, t0 + ahead, end);
+        }
+        if (++s == p.stages) {
+            s = 0;
+            phase ^= 1u;
         }
     }
+    if (qn) walk_queue<IDENT, BATCH, MODE>(p, queue, qn, gw, TW, end, k, s_lut, lane, acc, look);
 
     // warp reductions: single-text count and lookups
 #pragma unroll
@@ -589,14 +669,14 @@ KernelFn pick_kernel(uint32_t C, uint32_t k, bool batch, int mode)
 uint32_t round16(uint64_t x) { return (uint32_t)((x + 15) & ~15ull); }
 
 struct Layout {
-    uint32_t off_lut, off_warp, warp_bytes, off_queue, off_stages, stage_bytes, total;
-    uint32_t filt_u4, filt_words, halo;
+    uint32_t off_dense, off_lut, off_warp, warp_bytes, off_queue, off_stages, stage_bytes, total;
+    uint32_t filt_u4, dense_u4, filt_words, halo;
 };
 
 int width_index(int32_t bits) { return bits == 8 ? 0 : bits == 16 ? 1 : 2; }
 
-// Shared memory: [filter][class LUT] shared by the CTA, then one block per
-// warp: [mbarriers][walk queue][stages x (tile + halo)].
+// Shared memory: [filter][dense table][class LUT] shared by the CTA, then
+// one block per warp: [mbarriers][walk queue][stages x (tile + halo)].
 Layout layout(const TrieDev &t, const pm_config &cfg)
 {
     Layout L{};
@@ -604,13 +684,15 @@ Layout layout(const TrieDev &t, const pm_config &cfg)
     L.filt_words = t.filter_words[k][width_index(cfg.filter_bits)];
     L.filt_u4 = L.filt_words / 4;
     uint32_t off = round16((uint64_t)L.filt_words * 4);
+    L.off_dense = off;
+    L.dense_u4 = 0;
     L.off_lut = off;
     if (t.C != 256) off += 64 * 32 * 4;
     L.off_warp = off;
     L.halo = round16(t.max_len > 16 ? t.max_len : 16);
     L.stage_bytes = (uint32_t)cfg.tile + L.halo;
     L.off_queue = round16((uint64_t)kMaxStages * 8);
-    L.off_stages = L.off_queue + kQueue * 4;
+    L.off_stages = L.off_queue + kQueue * 8;
     L.warp_bytes = L.off_stages + (uint32_t)cfg.stages * L.stage_bytes;
     L.total = off + (uint32_t)(cfg.threads / 32) * L.warp_bytes;
     return L;
@@ -672,6 +754,7 @@ int launch_scan(const TrieDev &t, const pm_config &cfg, const ScanArgs &a, void 
     p.stages = (uint32_t)cfg.stages;
     p.aligned = ((uintptr_t)a.text & 15u) == 0;
     p.ids_aligned = ((uintptr_t)a.ids & 15u) == 0;
+    p.off_dense = L.off_dense;
     p.off_lut = L.off_lut;
     p.off_warp = L.off_warp;
     p.warp_bytes = L.warp_bytes;
@@ -679,6 +762,7 @@ int launch_scan(const TrieDev &t, const pm_config &cfg, const ScanArgs &a, void 
     p.off_stages = L.off_stages;
     p.stage_bytes = L.stage_bytes;
     p.filt_u4 = L.filt_u4;
+    p.dense_u4 = L.dense_u4;
     p.filt_words = L.filt_words;
 
     cudaError_t e;
