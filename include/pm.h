@@ -182,6 +182,34 @@ int pm_scan_ex(const pm_trie *h, const uint8_t *d_texts,
 int pm_scan_host(pm_trie *h, const uint8_t *h_text, uint64_t len,
                  int32_t *h_ids, int64_t *h_count);
 
+/* ---- host buffers, no device allocation ----------------------------------
+ * pm_scan_host_static: pm_scan_host for callers that cannot let a library
+ * allocate device memory: processes whose device memory belongs to one
+ * allocator (a framework's caching allocator, or an arena reserved up front)
+ * where a raw cudaMalloc/cudaFree would bypass or exceed it, and
+ * latency-sensitive callers for whom cudaMalloc/cudaFree add long, often
+ * device-synchronising stalls on the request path. The paper has no
+ * counterpart: this is a service of the library, not part of the method.
+ * The text (at most PM_STATIC_MAX_LEN bytes), its ids and its count are
+ * staged in one statically sized device array inside libpm (about 5 MiB,
+ * held on every GPU that loads the library until the process exits). No
+ * cudaMalloc, cudaFree or allocating library routine is called. The caller
+ * passes the host text h_text[0..len) and receives h_ids int32[len] and
+ * *h_count; the copies and the scan run on `stream` (NULL: the legacy
+ * default stream) and the call returns once the results are on the host.
+ * The first call on a device looks up the array's device address for that
+ * device (cudaGetSymbolAddress, with that device current); make that first
+ * call before any stream capture on the device.
+ * Every call uses the same array, which keeps the last call's contents;
+ * each call overwrites all its ids and zeroes the count first. Calls whose
+ * work overlaps on the GPU (other streams, other host threads) race on the
+ * array: serialise them.
+ * Errors: PM_ERR_INVAL (null pointers, len > PM_STATIC_MAX_LEN, current
+ * device is not the handle's), PM_ERR_HOST_ONLY, PM_ERR_CUDA. */
+#define PM_STATIC_MAX_LEN (1ull << 20)
+int pm_scan_host_static(const pm_trie *h, const uint8_t *h_text, uint64_t len,
+                        int32_t *h_ids, int64_t *h_count, pm_stream stream);
+
 /* ---- errors ------------------------------------------------------------ */
 /* Reads and clears the device-side error word (synchronises the device):
  * *code = PM_OK, PM_ERR_TIMEOUT or PM_ERR_BOUNDS. Errors: PM_ERR_CUDA. */

@@ -296,6 +296,15 @@ int scan_common(const pm_trie *h, const uint8_t *d_texts, const uint64_t *d_offs
 
 }  // namespace
 
+namespace pm {
+int set_last_error(int code, const std::string &msg)
+{
+    t_last = code;
+    t_msg = msg;
+    return code;
+}
+}  // namespace pm
+
 extern "C" {
 
 int pm_build(const uint8_t *const *patterns, const uint32_t *lengths, uint32_t n, pm_trie **out,

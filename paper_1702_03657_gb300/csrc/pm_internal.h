@@ -138,6 +138,9 @@ uint64_t scan_smem_bytes(const TrieDev &t, const pm_config &cfg);
 // Reads and clears the device error word.
 int read_device_error(int *code, std::string &msg);
 
+// Records `code` and `msg` as this thread's last error and returns `code`.
+int set_last_error(int code, const std::string &msg);
+
 }  // namespace pm
 
 // Opaque handle (C ABI type).

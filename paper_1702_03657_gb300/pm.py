@@ -26,12 +26,13 @@ PM_ERR_BUSY = -8
 PM_ERR_NOT_FOUND = -9
 PM_ERR_HOST_ONLY = -10
 PM_MAX_PATTERN_LEN = 4096
+PM_STATIC_MAX_LEN = 1 << 20
 
 # every symbol include/pm.h declares (checked by the tests)
 EXPORTS = (
     "pm_build", "pm_build_host", "pm_free", "pm_stats", "pm_export_csr",
     "pm_get_config", "pm_set_config", "pm_scan", "pm_scan_batch", "pm_scan_ex",
-    "pm_scan_host", "pm_device_error", "pm_strerror", "pm_last_error",
+    "pm_scan_host", "pm_scan_host_static", "pm_device_error", "pm_strerror", "pm_last_error",
     "pm_last_error_msg",
 )
 
@@ -102,6 +103,7 @@ def load(path: Optional[str] = None):
         "pm_scan_batch": ([P, P, P, u32, P, P, P], C.c_int),
         "pm_scan_ex": ([P, P, P, u32, u64, P, P, P, P, P], C.c_int),
         "pm_scan_host": ([P, P, u64, P, P], C.c_int),
+        "pm_scan_host_static": ([P, P, u64, P, P, P], C.c_int),
         "pm_device_error": ([P], C.c_int),
         "pm_strerror": ([C.c_int], C.c_char_p),
         "pm_last_error": ([], C.c_int),
@@ -274,6 +276,17 @@ def pm_scan_host(trie: Trie, text: np.ndarray, ids: np.ndarray) -> int:
     _check(load().pm_scan_host(trie.handle, text.ctypes.data if text.size else None,
                                text.size, ids.ctypes.data if ids.size else None,
                                C.byref(cnt)), "pm_scan_host")
+    return cnt.value
+
+
+def pm_scan_host_static(trie: Trie, text: np.ndarray, ids: np.ndarray, stream=None) -> int:
+    """pm_scan_host without any device allocation (text <= PM_STATIC_MAX_LEN
+    bytes, staged in libpm's static device array); returns the count."""
+    assert text.dtype == np.uint8 and ids.dtype == np.int32 and ids.size >= text.size
+    cnt = C.c_int64()
+    _check(load().pm_scan_host_static(trie.handle, text.ctypes.data if text.size else None,
+                                      text.size, ids.ctypes.data if ids.size else None,
+                                      C.byref(cnt), _stream_ptr(stream)), "pm_scan_host_static")
     return cnt.value
 
 
