@@ -153,6 +153,7 @@ void fill_dev_sizes(pm_trie *h)
         d.dense_words[k] = (uint32_t)(t.dense[k].size() / 2);
         d.first[k] = t.first[k];
         d.nlevel[k] = t.nlevel[k];
+        d.gram[k] = t.gram[k];
         for (int w = 0; w < pm::kFilterWidths; ++w)
             d.filter_words[k][w] = (uint32_t)t.filter[k][w].size();
     }

@@ -196,25 +196,29 @@ int build_host_trie(const uint8_t *const *patterns, const uint32_t *lengths,
     // filter is indexed instead by the little-endian path (first byte least
     // significant), which the kernel reads straight from the text.
     const bool le = t.C == 256;
+    // depth of the paths the filters are built from: up to K+2 (Bloom)
+    const uint32_t D = le ? K + 2 : K + 1;
     std::vector<uint64_t> code(nn, 0), fcode(nn, 0);
     for (uint32_t v = 0; v < nn; ++v) {
-        if (t.depth[v] > K) break;  // BFS: depths never decrease
+        if (t.depth[v] >= D) break;  // BFS: depths never decrease
         for (uint32_t e = t.row_ptr[v]; e < t.row_ptr[v + 1]; ++e) {
             code[t.next[e]] = code[v] * t.C + t.cls[t.col[e]];
             fcode[t.next[e]] = le ? fcode[v] | ((uint64_t)t.col[e] << (8 * t.depth[v]))
                                   : code[t.next[e]];
         }
     }
-    std::vector<uint32_t> lvl_begin(K + 2, nn), lvl_count(K + 2, 0);
+    std::vector<uint32_t> lvl_begin(K + 3, nn), lvl_count(K + 3, 0);
     for (uint32_t v = 0; v < nn; ++v) {
         uint32_t d = t.depth[v];
-        if (d > K + 1) break;
+        if (d > K + 2) break;
         if (lvl_count[d]++ == 0) lvl_begin[d] = v;
     }
     for (uint32_t k = 0; k <= K; ++k) {
         const uint64_t codes = ipow_capped(t.C, (int)k, ~0ull);
         t.first[k] = lvl_count[k] ? lvl_begin[k] : 0;
         t.nlevel[k] = lvl_count[k];
+        // a Bloom level may test k+2 bytes only if no pattern ends at k+1
+        t.gram[k] = (le && k >= kBloomK && k + 2 <= 4 && t.min_len >= k + 2) ? k + 2 : k + 1;
         if (k >= 1) {
             uint64_t words = (codes + 31) / 32;
             words += words & 1;  // even: copied in 16-byte units
@@ -245,11 +249,13 @@ int build_host_trie(const uint8_t *const *patterns, const uint32_t *lengths,
             std::vector<uint32_t> &f = t.filter[k][wi];
             f.assign(words, 0);
             if (le && k >= kBloomK) {
-                // byte alphabet, k >= 2: blocked Bloom filter of the paths of
-                // length k+1 (read little-endian) over 2^(8k + log2 W) bits
+                // byte alphabet, k >= 2: blocked Bloom filter of the root
+                // paths of length g (read little-endian) over 2^(8k + log2 W)
+                // bits; g = k+2 when no pattern ends at depth k+1
+                const uint32_t g = t.gram[k];
                 const uint32_t word_bits = 8 * k + (3 + wi) - 5;
-                for (uint32_t i = 0; i < lvl_count[k + 1]; ++i) {
-                    const BloomProbe b = bloom_probe((uint32_t)fcode[lvl_begin[k + 1] + i], word_bits);
+                for (uint32_t i = 0; i < lvl_count[g]; ++i) {
+                    const BloomProbe b = bloom_probe((uint32_t)fcode[lvl_begin[g] + i], g, word_bits);
                     f[b.word] |= b.mask;
                 }
                 continue;

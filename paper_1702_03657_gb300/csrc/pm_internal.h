@@ -44,22 +44,28 @@ constexpr int kFilterWidths = 3;
 // as uint2 {bits, base} per 32 codes.
 //
 // Byte alphabet with k >= kBloomK: the filter is instead a blocked Bloom
-// filter over 2^(8k + log2 W) bits of the paths of length k+1, each read as
-// the little-endian integer x = sum_j b_j << 8j. One multiplicative hash
-// h = hi32((x << 8) * M) picks a 32-bit word (its top bits) and two bits in
-// it (its low 10 bits); both are set for every such path. A clear bit
-// proves that the (k+1)-gram is not a root path. The depth-k node is then
-// looked up in the dense table, which also tells whether the k-gram itself
-// is a path.
+// filter over 2^(8k + log2 W) bits of the root paths of length g (g = k+2
+// when every pattern is longer than k+1, else k+1), each read as the
+// little-endian integer x = sum_j b_j << 8j. One multiplicative hash
+// h = hi32((x << (32 - 8g)) * M) picks a 32-bit word (its top bits) and
+// two bits in it (h mod 32 and (h >> 5) mod 32); both are set for every such path. A
+// clear bit proves that the g-gram is not a root path, so the walk stops at
+// depth <= g-1 < shortest pattern. The depth-k node of a passing position is
+// then looked up in the dense table, which also tells whether the k-gram
+// itself is a path.
 constexpr uint32_t kBloomK = 2;
 constexpr uint32_t kBloomMul = 0x9E3779B1u;  // Knuth's golden-ratio multiplier
 struct BloomProbe {
     uint32_t word, mask;
 };
-__host__ __device__ inline BloomProbe bloom_probe(uint32_t x, uint32_t word_bits)
+__host__ __device__ inline uint32_t bloom_mask(uint32_t h)
 {
-    const uint32_t h = (uint32_t)(((uint64_t)(x << 8) * kBloomMul) >> 32);
-    return {h >> (32u - word_bits), (1u << (h & 31u)) | (1u << ((h >> 5) & 31u))};
+    return (1u << (h & 31u)) | (1u << ((h >> 5) & 31u));
+}
+__host__ __device__ inline BloomProbe bloom_probe(uint32_t x, uint32_t gram, uint32_t word_bits)
+{
+    const uint32_t h = (uint32_t)(((uint64_t)(x << (32u - 8u * gram)) * kBloomMul) >> 32);
+    return {h >> (32u - word_bits), bloom_mask(h)};
 }
 
 // Filter of level k and width W (shared memory): a bitset of C^k * W bits.
@@ -83,6 +89,7 @@ struct TrieDev {
     uint32_t dense_words[kMaxDenseK + 1];                 // uint2 entries of table k
     uint32_t first[kMaxDenseK + 1];                       // BFS id of the first depth-k node
     uint32_t nlevel[kMaxDenseK + 1];                      // number of depth-k nodes
+    uint32_t gram[kMaxDenseK + 1];                        // bytes a level-k filter tests
     uint32_t C;                                           // classes
     uint32_t n_nodes;
     uint32_t nnz;
@@ -109,6 +116,7 @@ struct HostTrie {
     std::vector<uint32_t> filter[kMaxDenseK + 1][kFilterWidths];
     uint32_t first[kMaxDenseK + 1] = {};
     uint32_t nlevel[kMaxDenseK + 1] = {};
+    uint32_t gram[kMaxDenseK + 1] = {};  // bytes a level-k filter tests: k+1 or k+2
 };
 
 // Builds the host trie. Returns PM_OK or an error code (msg filled).

@@ -59,6 +59,7 @@ struct KParams {
     const uint32_t *filter;     // filter table of level k, width W (global)
     const uint2 *dense;         // dense table of level k (k >= 1, global)
     uint32_t first_k;           // BFS id of the first depth-k node
+    uint32_t gram;              // bytes the filter tests per position (k+1 or k+2)
     uint32_t tile;
     uint32_t halo;
     uint32_t k;
@@ -253,7 +254,7 @@ __device__ __forceinline__ uint32_t crs_walk(const TrieDev &t, const uint8_t *te
         if (c0 > b || r1 - r0 == 1) break;
         uint32_t e;
         bool found = false;
-        if (binary) {
+        if (binary || r1 - r0 > 16) {  // long rows are always searched by halving
             uint32_t lo = r0 + 1, hi = r1;
             while (lo < hi) {
                 const uint32_t mid = (lo + hi) >> 1;
@@ -358,8 +359,9 @@ __device__ __forceinline__ void walk_queue(const KParams &p, const uint2 *queue,
 }
 
 // KF: the filter level k when fixed at compile time (byte alphabet), or -1
-// for a runtime k over byte classes.
-template <int KF, bool IDENT, bool BATCH, int MODE>
+// for a runtime k over byte classes. G: bytes the byte-alphabet Bloom filter
+// tests (3 or 4), 0 when not fixed.
+template <int KF, int G, bool IDENT, bool BATCH, int MODE>
 __global__ void __launch_bounds__(1024, 1) pfac_scan_kernel(const KParams p)
 {
     extern __shared__ __align__(16) uint8_t smem[];
@@ -414,6 +416,7 @@ __global__ void __launch_bounds__(1024, 1) pfac_scan_kernel(const KParams p)
     __syncwarp();
 
     const uint32_t k = KF >= 0 ? (uint32_t)KF : p.k;
+    const uint32_t gram = p.gram;
     const uint32_t C = t.C;
     const uint32_t lw = p.lw;
     const uint32_t wmask = (1u << lw) - 1u;
@@ -458,7 +461,7 @@ __global__ void __launch_bounds__(1024, 1) pfac_scan_kernel(const KParams p)
         uint32_t rel_end = rel_end_of(text_end, t0);
         // groups [lp0, lp0+4) with lp0 + 4 <= fast_n take the fast path
         auto fast_bound = [&]() -> uint32_t {
-            const uint32_t r = rel_end >= k ? rel_end - k : 0u;
+            const uint32_t r = rel_end >= gram - 1 ? rel_end - (gram - 1) : 0u;
             return r < tile_n ? r : tile_n;
         };
         uint32_t fast_n = fast_bound();
@@ -486,19 +489,22 @@ __global__ void __launch_bounds__(1024, 1) pfac_scan_kernel(const KParams p)
                     // blocked Bloom test of the (k+1)-gram at each position
                     const uint32_t w0 = wp[0], w1 = wp[1];
                     const uint32_t sh = 32u - (8u * KF + lw - 5u);
+                    const uint32_t gsh = G > 0 ? 32u - 8u * G : 32u - 8u * gram;
 #pragma unroll
                     for (int q = 0; q < 4; ++q) {
                         const uint32_t win = q == 0 ? w0 : __funnelshift_r(w0, w1, 8 * q);
-                        // bytes q .. q+k, shifted to the top (x << 8)
-                        const uint32_t x8 = win << (24 - 8 * KF);
-                        const uint32_t h = __umulhi(x8, kBloomMul);
+                        // bytes q .. q+g-1, shifted to the top
+                        const uint32_t h = __umulhi(G == 4 ? win : win << gsh, kBloomMul);
                         const uint32_t word = h >> sh;
-                        const uint32_t mask = (1u << (h & 31u)) | (1u << ((h >> 5) & 31u));
                         if (MODE == MODE_CHECKED && word >= p.filt_words) {
                             record_error(PM_ERR_BOUNDS);
                             continue;
                         }
-                        need |= (uint32_t)((s_filt[word] & mask) == mask) << q;
+                        // both Bloom bits, each rotated down to bit 0 (the
+                        // funnel shift takes its amount mod 32)
+                        const uint32_t val = s_filt[word];
+                        const uint32_t r = __funnelshift_r(val, val, h) & __funnelshift_r(val, val, h >> 5);
+                        need |= (r & 1u) << q;
                     }
                 } else if (IDENT && KF >= 0) {
                     const uint32_t w0 = wp[0];
@@ -557,15 +563,15 @@ __global__ void __launch_bounds__(1024, 1) pfac_scan_kernel(const KParams p)
                         rel_end = rel_end_of(text_end, t0);
                         fast_n = fast_bound();
                     }
-                    if (MODE == MODE_LOOKUPS || lp + k + 1 > rel_end) {
+                    if (MODE == MODE_LOOKUPS || lp + gram > rel_end) {
                         rootm |= 1u << q;
                         continue;
                     }
                     uint32_t word, bits;
                     if (IDENT && KF >= (int)kBloomK) {
                         uint32_t x = 0;
-                        for (uint32_t j = 0; j <= k; ++j) x |= (uint32_t)st[lp + j] << (8 * j);
-                        const BloomProbe b = bloom_probe(x, 8u * KF + lw - 5u);
+                        for (uint32_t j = 0; j < gram; ++j) x |= (uint32_t)st[lp + j] << (8 * j);
+                        const BloomProbe b = bloom_probe(x, gram, 8u * KF + lw - 5u);
                         word = b.word;
                         bits = b.mask;
                     } else if (IDENT && KF >= 0) {
@@ -638,32 +644,34 @@ __global__ void __launch_bounds__(1024, 1) pfac_scan_kernel(const KParams p)
 
 typedef void (*KernelFn)(KParams);
 
-template <int KF, bool IDENT>
+template <int KF, int G, bool IDENT>
 KernelFn pick_mode(bool batch, int mode)
 {
     if (batch) {
         switch (mode) {
-        case MODE_CHECKED: return pfac_scan_kernel<KF, IDENT, true, MODE_CHECKED>;
-        case MODE_LOOKUPS: return pfac_scan_kernel<KF, IDENT, true, MODE_LOOKUPS>;
-        default: return pfac_scan_kernel<KF, IDENT, true, MODE_FAST>;
+        case MODE_CHECKED: return pfac_scan_kernel<KF, G, IDENT, true, MODE_CHECKED>;
+        case MODE_LOOKUPS: return pfac_scan_kernel<KF, G, IDENT, true, MODE_LOOKUPS>;
+        default: return pfac_scan_kernel<KF, G, IDENT, true, MODE_FAST>;
         }
     }
     switch (mode) {
-    case MODE_CHECKED: return pfac_scan_kernel<KF, IDENT, false, MODE_CHECKED>;
-    case MODE_LOOKUPS: return pfac_scan_kernel<KF, IDENT, false, MODE_LOOKUPS>;
-    default: return pfac_scan_kernel<KF, IDENT, false, MODE_FAST>;
+    case MODE_CHECKED: return pfac_scan_kernel<KF, G, IDENT, false, MODE_CHECKED>;
+    case MODE_LOOKUPS: return pfac_scan_kernel<KF, G, IDENT, false, MODE_LOOKUPS>;
+    default: return pfac_scan_kernel<KF, G, IDENT, false, MODE_FAST>;
     }
 }
 
-// Byte alphabet (C = 256): k is 0, 1 or 2 and fixed at compile time.
-KernelFn pick_kernel(uint32_t C, uint32_t k, bool batch, int mode)
+// Byte alphabet (C = 256): k is 0, 1 or 2 and fixed at compile time, and so
+// is the Bloom gram length at k = 2.
+KernelFn pick_kernel(uint32_t C, uint32_t k, uint32_t gram, bool batch, int mode)
 {
     if (C == 256) {
-        if (k == 0) return pick_mode<0, true>(batch, mode);
-        if (k == 1) return pick_mode<1, true>(batch, mode);
-        return pick_mode<2, true>(batch, mode);
+        if (k == 0) return pick_mode<0, 0, true>(batch, mode);
+        if (k == 1) return pick_mode<1, 0, true>(batch, mode);
+        if (gram == 4) return pick_mode<2, 4, true>(batch, mode);
+        return pick_mode<2, 3, true>(batch, mode);
     }
-    return pick_mode<-1, false>(batch, mode);
+    return pick_mode<-1, 0, false>(batch, mode);
 }
 
 uint32_t round16(uint64_t x) { return (uint32_t)((x + 15) & ~15ull); }
@@ -730,7 +738,7 @@ int launch_scan(const TrieDev &t, const pm_config &cfg, const ScanArgs &a, void 
     if (batch ? a.ntexts == 0 : a.len == 0) return PM_OK;
 
     const int mode = a.lookups ? MODE_LOOKUPS : (cfg.checked ? MODE_CHECKED : MODE_FAST);
-    KernelFn fn = pick_kernel(t.C, (uint32_t)cfg.dense_k, batch, mode);
+    KernelFn fn = pick_kernel(t.C, (uint32_t)cfg.dense_k, t.gram[cfg.dense_k], batch, mode);
     Layout L = layout(t, cfg);
 
     KParams p{};
@@ -750,6 +758,7 @@ int launch_scan(const TrieDev &t, const pm_config &cfg, const ScanArgs &a, void 
     p.filter = t.filter[cfg.dense_k][width_index(cfg.filter_bits)];
     p.dense = cfg.dense_k > 0 ? t.dense[cfg.dense_k] : nullptr;
     p.first_k = t.first[cfg.dense_k];
+    p.gram = t.gram[cfg.dense_k];
     p.binary = cfg.row_search ? 1u : 0u;
     p.stages = (uint32_t)cfg.stages;
     p.aligned = ((uintptr_t)a.text & 15u) == 0;
