@@ -210,6 +210,83 @@ int pm_scan_host(pm_trie *h, const uint8_t *h_text, uint64_t len,
 int pm_scan_host_static(const pm_trie *h, const uint8_t *h_text, uint64_t len,
                         int32_t *h_ids, int64_t *h_count, pm_stream stream);
 
+/* ---- serving: continuous batching (SURVEY north star (b); the paper has a
+ * single batch-free scan, Section II-C) ------------------------------------
+ * A server keeps the trie resident and runs a scheduler thread that
+ *  - admits submitted requests in arrival order as batch slots and device
+ *    memory (a first-fit arena for request texts) free up,
+ *  - launches everything admitted at that moment as one batched scan (one
+ *    persistent kernel over a device offset table) whose ids and counts go
+ *    straight to each request's own device buffers,
+ *  - runs up to max_inflight batches at once, each on its own stream, so new
+ *    requests overlap with those already on the GPU,
+ *  - marks requests done when their batch's event completes.
+ * Results are bit-identical to scanning each request alone with pm_scan. */
+typedef struct pm_server pm_server;
+
+typedef struct {
+    uint64_t arena_bytes;     /* device bytes for texts in flight (0: 256 MiB)  */
+    uint32_t max_inflight;    /* batches on the GPU at once, 1..64 (0: 4)       */
+    uint32_t max_batch;       /* requests per batch (0: 1024)                   */
+    uint64_t max_batch_bytes; /* text bytes per batch, a larger single request  */
+                              /* still runs alone (0: 64 MiB)                   */
+    uint32_t max_queue;       /* submitted, not yet admitted (0: 65536)         */
+} pm_server_config;
+
+typedef struct {
+    uint64_t submitted, completed, batches, bytes;
+    uint64_t max_batch_seen;     /* most requests in one batch                 */
+    uint64_t max_inflight_seen;  /* most batches on the GPU at once            */
+    uint64_t admission_waits;    /* times a request waited for arena memory    */
+} pm_server_stats;
+
+/* Creates a server for a built trie (device handle) on the current device,
+ * which must be the trie's. cfg may be NULL (defaults). The handle must
+ * outlive the server. Errors: PM_ERR_INVAL, PM_ERR_HOST_ONLY, PM_ERR_NOMEM. */
+int pm_server_create(const pm_trie *h, const pm_server_config *cfg, pm_server **out);
+
+/* Queues a scan of the HOST text h_text[0..len) (it must stay valid and
+ * unchanged until the request is done; pinned memory copies fastest) with
+ * results to caller-owned DEVICE buffers out.ids int32[len] and out.count
+ * int64[1]. Returns at once with *req_id. Thread-safe.
+ * Errors: PM_ERR_INVAL (NULLs, len > arena_bytes), PM_ERR_BUSY (queue full),
+ * PM_ERR_CUDA (the server failed). */
+int pm_submit(pm_server *s, const uint8_t *h_text, uint64_t len, pm_result out,
+              uint64_t *req_id);
+
+/* *done = 1 once the request's results are in its buffers; a done request
+ * is reported once and then forgotten. Errors: PM_ERR_NOT_FOUND, or the
+ * request's own error (PM_ERR_CUDA). */
+int pm_poll(pm_server *s, uint64_t req_id, int *done);
+
+/* Blocks until the request is done or timeout_ms passes (PM_ERR_TIMEOUT);
+ * then as pm_poll with done = 1. */
+int pm_wait(pm_server *s, uint64_t req_id, uint32_t timeout_ms);
+
+int pm_server_get_stats(pm_server *s, pm_server_stats *st);
+
+/* Finishes every submitted request, stops the scheduler and frees the
+ * server's memory. Returns PM_ERR_CUDA if the server had failed. */
+int pm_server_destroy(pm_server *s);
+
+/* Trace replay for benchmarks, timed natively: request i (host text
+ * h_texts[i], lens[i] bytes, outputs d_ids[i], d_counts[i]) is submitted at
+ * arrival_ns[i] after the start; latency_ns[i] = completion seen on the host
+ * minus that scheduled arrival; *wall_ns = start to the last completion. */
+int pm_server_replay(pm_server *s, uint32_t n, const uint8_t *const *h_texts,
+                     const uint64_t *lens, const uint64_t *arrival_ns,
+                     int32_t *const *d_ids, int64_t *const *d_counts,
+                     uint64_t *latency_ns, uint64_t *wall_ns);
+
+/* The same trace served plainly: each request, at its arrival, is copied to
+ * its own device buffer d_texts[i] and scanned by its own pm_scan launch on
+ * `stream` (no batching, no overlap beyond one stream). */
+int pm_replay_plain(const pm_trie *h, uint32_t n, const uint8_t *const *h_texts,
+                    const uint64_t *lens, const uint64_t *arrival_ns,
+                    uint8_t *const *d_texts, int32_t *const *d_ids,
+                    int64_t *const *d_counts, uint64_t *latency_ns,
+                    uint64_t *wall_ns, pm_stream stream);
+
 /* ---- errors ------------------------------------------------------------ */
 /* Reads and clears the device-side error word (synchronises the device):
  * *code = PM_OK, PM_ERR_TIMEOUT or PM_ERR_BOUNDS. Errors: PM_ERR_CUDA. */

@@ -134,6 +134,14 @@ struct ScanArgs {
     int32_t *ids;
     int64_t *counts;
     unsigned long long *lookups;  // optional
+    // batch only, optional: per-text output buffers (device arrays of device
+    // pointers); ids of text t go to out_ids[t][0 .. len_t), and counts[t]
+    // (still required, internal) is copied to *out_counts[t] at the end
+    int32_t *const *out_ids;
+    int64_t *const *out_counts;
+    // batch only, optional: total text bytes when the host knows it (sizes
+    // the persistent grid to the work; 0: one CTA per SM)
+    uint64_t total_hint;
 };
 
 // Enqueues the scan (counts zeroed first). Returns PM_OK / PM_ERR_CUDA.

@@ -54,6 +54,7 @@ struct KParams {
     unsigned long long total;   // single text: start positions to scan
     unsigned long long limit;   // single text: readable bytes (>= total)
     int32_t *ids;
+    int32_t *const *out_ids;    // batch: per-text id buffers (nullptr: ids + offset)
     int64_t *counts;
     unsigned long long *lookups;
     const uint32_t *filter;     // filter table of level k, width W (global)
@@ -345,7 +346,10 @@ __device__ __forceinline__ void walk_queue(const KParams &p, const uint2 *queue,
             if (j - pos >= t.min_len) {
                 const int2 em = __ldg(t.emit + v);
                 if (em.y) {
-                    p.ids[pos] = em.x;
+                    if (BATCH && p.out_ids)
+                        p.out_ids[txt][pos - __ldg(p.offsets + txt)] = em.x;
+                    else
+                        p.ids[pos] = em.x;
                     if (BATCH)
                         atomicAdd(reinterpret_cast<unsigned long long *>(p.counts + txt),
                                   (unsigned long long)em.y);
@@ -415,7 +419,8 @@ __global__ void __launch_bounds__(1024, 1) pfac_scan_kernel(const KParams p)
     }
     __syncwarp();
 
-    const uint32_t k = KF >= 0 ? (uint32_t)KF : p.k;
+    constexpr uint32_t KFU = KF > 0 ? (uint32_t)KF : 0u;  // KF as unsigned (0 if runtime)
+    const uint32_t k = KF >= 0 ? KFU : p.k;
     const uint32_t gram = p.gram;
     const uint32_t C = t.C;
     const uint32_t lw = p.lw;
@@ -479,6 +484,7 @@ __global__ void __launch_bounds__(1024, 1) pfac_scan_kernel(const KParams p)
                 rel_end = rel_end_of(text_end, t0);
                 fast_n = fast_bound();
             }
+            const uint32_t cur0 = cur;  // text of position lp0
             uint32_t need = 0;   // bit q: position lp0+q passed the filter
             uint32_t rootm = 0;  // bit q: position lp0+q is walked from the root
             if (MODE != MODE_LOOKUPS && lp0 + 4 <= fast_n) {
@@ -488,7 +494,7 @@ __global__ void __launch_bounds__(1024, 1) pfac_scan_kernel(const KParams p)
                 if (IDENT && KF >= (int)kBloomK) {
                     // blocked Bloom test of the (k+1)-gram at each position
                     const uint32_t w0 = wp[0], w1 = wp[1];
-                    const uint32_t sh = 32u - (8u * KF + lw - 5u);
+                    const uint32_t sh = 32u - (8u * KFU + lw - 5u);
                     const uint32_t gsh = G > 0 ? 32u - 8u * G : 32u - 8u * gram;
 #pragma unroll
                     for (int q = 0; q < 4; ++q) {
@@ -571,7 +577,7 @@ __global__ void __launch_bounds__(1024, 1) pfac_scan_kernel(const KParams p)
                     if (IDENT && KF >= (int)kBloomK) {
                         uint32_t x = 0;
                         for (uint32_t j = 0; j < gram; ++j) x |= (uint32_t)st[lp + j] << (8 * j);
-                        const BloomProbe b = bloom_probe(x, gram, 8u * KF + lw - 5u);
+                        const BloomProbe b = bloom_probe(x, gram, 8u * KFU + lw - 5u);
                         word = b.word;
                         bits = b.mask;
                     } else if (IDENT && KF >= 0) {
@@ -582,7 +588,7 @@ __global__ void __launch_bounds__(1024, 1) pfac_scan_kernel(const KParams p)
                         bits = 1u << (idx & 31u);
                     } else {
                         uint32_t cd = 0;
-                        for (uint32_t j = 0; j < k; ++j) cd = cd * C + class_of<IDENT>(s_lut, lane, st[lp + j]);
+                        for (uint32_t j = 0; j + 1 <= k; ++j) cd = cd * C + class_of<IDENT>(s_lut, lane, st[lp + j]);
                         const uint32_t idx = (cd << lw) | (class_of<IDENT>(s_lut, lane, st[lp + k]) & wmask);
                         word = idx >> 5;
                         bits = 1u << (idx & 31u);
@@ -595,7 +601,19 @@ __global__ void __launch_bounds__(1024, 1) pfac_scan_kernel(const KParams p)
                 }
             }
             // every position gets -1 now; phase 2 patches the matches
-            if (p.ids_aligned && lp0 + 4 <= tile_n) {
+            if (BATCH && p.out_ids) {
+                // per-text output buffers: each position to its own text's
+                uint32_t c2 = cur0;
+                unsigned long long e2 = __ldg(p.offsets + c2 + 1);
+                for (uint32_t q = 0; q < 4 && lp0 + q < tile_n; ++q) {
+                    const unsigned long long pos = t0 + lp0 + q;
+                    while (pos >= e2) {
+                        ++c2;
+                        e2 = __ldg(p.offsets + c2 + 1);
+                    }
+                    __stcs(p.out_ids[c2] + (pos - __ldg(p.offsets + c2)), -1);
+                }
+            } else if (p.ids_aligned && lp0 + 4 <= tile_n) {
                 __stcs(reinterpret_cast<int4 *>(idt + lp0), make_int4(-1, -1, -1, -1));
             } else {
 #pragma unroll
@@ -674,6 +692,13 @@ KernelFn pick_kernel(uint32_t C, uint32_t k, uint32_t gram, bool batch, int mode
     return pick_mode<-1, 0, false>(batch, mode);
 }
 
+// Per-text count finalisation: counts[t] to the caller's *out[t].
+__global__ void pm_counts_scatter_kernel(const int64_t *counts, int64_t *const *out, uint32_t n)
+{
+    const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < n) *out[t] = counts[t];
+}
+
 uint32_t round16(uint64_t x) { return (uint32_t)((x + 15) & ~15ull); }
 
 struct Layout {
@@ -749,6 +774,7 @@ int launch_scan(const TrieDev &t, const pm_config &cfg, const ScanArgs &a, void 
     p.total = a.len;
     p.limit = a.limit > a.len ? a.limit : a.len;
     p.ids = a.ids;
+    p.out_ids = a.out_ids;
     p.counts = a.counts;
     p.lookups = a.lookups;
     p.tile = (uint32_t)cfg.tile;
@@ -795,9 +821,10 @@ int launch_scan(const TrieDev &t, const pm_config &cfg, const ScanArgs &a, void 
     }
     if (cfg.ctas_per_sm > 0 && cfg.ctas_per_sm < occ) occ = cfg.ctas_per_sm;
     unsigned long long grid = (unsigned long long)device_sms * occ;
-    if (!batch) {
+    const unsigned long long known = batch ? a.total_hint : a.len;
+    if (known) {
         const unsigned long long warps = cfg.threads / 32;
-        unsigned long long ntiles = (a.len + cfg.tile - 1) / cfg.tile;
+        unsigned long long ntiles = (known + cfg.tile - 1) / cfg.tile;
         unsigned long long need = (ntiles + warps - 1) / warps;
         if (need < grid) grid = need;
     }
@@ -806,6 +833,15 @@ int launch_scan(const TrieDev &t, const pm_config &cfg, const ScanArgs &a, void 
     if (e != cudaSuccess) {
         msg = std::string("scan launch: ") + cudaGetErrorString(e);
         return PM_ERR_CUDA;
+    }
+    if (batch && a.out_counts) {
+        pm_counts_scatter_kernel<<<(a.ntexts + 255) / 256, 256, 0, st>>>(a.counts, a.out_counts,
+                                                                         a.ntexts);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) {
+            msg = std::string("count scatter launch: ") + cudaGetErrorString(e);
+            return PM_ERR_CUDA;
+        }
     }
     return PM_OK;
 }

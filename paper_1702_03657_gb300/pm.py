@@ -33,7 +33,8 @@ EXPORTS = (
     "pm_build", "pm_build_host", "pm_free", "pm_stats", "pm_export_csr",
     "pm_get_config", "pm_set_config", "pm_scan", "pm_scan_batch", "pm_scan_ex",
     "pm_scan_host", "pm_scan_host_static", "pm_device_error", "pm_strerror", "pm_last_error",
-    "pm_last_error_msg",
+    "pm_last_error_msg", "pm_server_create", "pm_submit", "pm_poll", "pm_wait",
+    "pm_server_get_stats", "pm_server_destroy", "pm_server_replay", "pm_replay_plain",
 )
 
 
@@ -57,6 +58,21 @@ class pm_trie_stats(C.Structure):
         ("dense256_bytes", C.c_uint64), ("bitmap36_bytes", C.c_uint64),
         ("device_bytes", C.c_uint64),
     ]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class pm_server_config(C.Structure):
+    _fields_ = [("arena_bytes", C.c_uint64), ("max_inflight", C.c_uint32),
+                ("max_batch", C.c_uint32), ("max_batch_bytes", C.c_uint64),
+                ("max_queue", C.c_uint32)]
+
+
+class pm_server_stats(C.Structure):
+    _fields_ = [(f, C.c_uint64) for f in (
+        "submitted", "completed", "batches", "bytes", "max_batch_seen",
+        "max_inflight_seen", "admission_waits")]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -108,6 +124,14 @@ def load(path: Optional[str] = None):
         "pm_strerror": ([C.c_int], C.c_char_p),
         "pm_last_error": ([], C.c_int),
         "pm_last_error_msg": ([], C.c_char_p),
+        "pm_server_create": ([P, P, P], C.c_int),
+        "pm_submit": ([P, P, u64, pm_result, P], C.c_int),
+        "pm_poll": ([P, u64, P], C.c_int),
+        "pm_wait": ([P, u64, u32], C.c_int),
+        "pm_server_get_stats": ([P, P], C.c_int),
+        "pm_server_destroy": ([P], C.c_int),
+        "pm_server_replay": ([P, u32, P, P, P, P, P, P, P], C.c_int),
+        "pm_replay_plain": ([P, u32, P, P, P, P, P, P, P, P, P], C.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -288,6 +312,92 @@ def pm_scan_host_static(trie: Trie, text: np.ndarray, ids: np.ndarray, stream=No
                                       text.size, ids.ctypes.data if ids.size else None,
                                       C.byref(cnt), _stream_ptr(stream)), "pm_scan_host_static")
     return cnt.value
+
+
+class Server:
+    """Owns a pm_server handle (destroyed with pm_server_destroy)."""
+
+    def __init__(self, handle, trie):
+        self.handle = handle
+        self.trie = trie  # the trie must outlive the server
+
+    def __del__(self):
+        h, self.handle = getattr(self, "handle", None), None
+        if h and _lib is not None:
+            _lib.pm_server_destroy(h)
+
+
+def pm_server_create(trie: Trie, arena_bytes=0, max_inflight=0, max_batch=0,
+                     max_batch_bytes=0, max_queue=0) -> Server:
+    cfg = pm_server_config(arena_bytes, max_inflight, max_batch, max_batch_bytes, max_queue)
+    h = C.c_void_p()
+    _check(load().pm_server_create(trie.handle, C.byref(cfg), C.byref(h)), "pm_server_create")
+    return Server(h.value, trie)
+
+
+def pm_submit(srv: Server, h_text: np.ndarray, ids, count) -> int:
+    """Queue a host text (numpy uint8, kept alive and unchanged by the caller
+    until done) with device outputs ids (int32[len]) and count (int64[1])."""
+    import torch
+    rid = C.c_uint64()
+    out = pm_result(_dptr(ids, torch.int32, "ids"), _dptr(count, torch.int64, "count"))
+    _check(load().pm_submit(srv.handle, h_text.ctypes.data if h_text.size else None,
+                            h_text.size, out, C.byref(rid)), "pm_submit")
+    return rid.value
+
+
+def pm_poll(srv: Server, req_id: int) -> bool:
+    done = C.c_int()
+    _check(load().pm_poll(srv.handle, req_id, C.byref(done)), "pm_poll")
+    return bool(done.value)
+
+
+def pm_wait(srv: Server, req_id: int, timeout_ms: int = 10000):
+    _check(load().pm_wait(srv.handle, req_id, timeout_ms), "pm_wait")
+
+
+def pm_server_get_stats(srv: Server) -> dict:
+    st = pm_server_stats()
+    _check(load().pm_server_get_stats(srv.handle, C.byref(st)), "pm_server_get_stats")
+    return st.as_dict()
+
+
+def pm_server_destroy(srv: Server):
+    h, srv.handle = srv.handle, None
+    if h:
+        _check(load().pm_server_destroy(h), "pm_server_destroy")
+
+
+def _ptr_array(ptrs):
+    return (C.c_void_p * max(len(ptrs), 1))(*ptrs)
+
+
+def pm_server_replay(srv: Server, h_ptrs, lens, arrival_ns, id_ptrs, count_ptrs):
+    """Native trace replay; returns (latency_ns array, wall_ns)."""
+    n = len(lens)
+    lens = np.ascontiguousarray(lens, dtype=np.uint64)
+    arr = np.ascontiguousarray(arrival_ns, dtype=np.uint64)
+    lat = np.zeros(n, dtype=np.uint64)
+    wall = C.c_uint64()
+    _check(load().pm_server_replay(srv.handle, n, _ptr_array(h_ptrs), lens.ctypes.data,
+                                   arr.ctypes.data, _ptr_array(id_ptrs),
+                                   _ptr_array(count_ptrs), lat.ctypes.data, C.byref(wall)),
+           "pm_server_replay")
+    return lat, wall.value
+
+
+def pm_replay_plain(trie: Trie, h_ptrs, lens, arrival_ns, text_ptrs, id_ptrs, count_ptrs,
+                    stream=None):
+    n = len(lens)
+    lens = np.ascontiguousarray(lens, dtype=np.uint64)
+    arr = np.ascontiguousarray(arrival_ns, dtype=np.uint64)
+    lat = np.zeros(n, dtype=np.uint64)
+    wall = C.c_uint64()
+    _check(load().pm_replay_plain(trie.handle, n, _ptr_array(h_ptrs), lens.ctypes.data,
+                                  arr.ctypes.data, _ptr_array(text_ptrs), _ptr_array(id_ptrs),
+                                  _ptr_array(count_ptrs), lat.ctypes.data, C.byref(wall),
+                                  _stream_ptr(stream)), "pm_replay_plain")
+    return lat, wall.value
 
 
 def pm_device_error() -> int:

@@ -133,3 +133,10 @@ def test_config_validation(lib):
         with pytest.raises(pm.PMError) as e:
             pm.pm_set_config(t, c)
         assert e.value.code == pm.PM_ERR_INVAL
+
+
+def test_server_rejects_host_only_trie(lib):
+    t = pm.pm_build_host([b"abc", b"abd"])
+    with pytest.raises(pm.PMError) as e:
+        pm.pm_server_create(t)
+    assert e.value.code == pm.PM_ERR_HOST_ONLY

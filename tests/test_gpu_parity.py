@@ -354,3 +354,18 @@ def test_acgt_full_size():
     check_windows(ot, wl.text, ids, sampled_windows(len(wl.text), 32, 4096, 2))
     _, o_cnt, _ = ot.scan(wl.text, threads=HOST_THREADS)
     assert cnt == o_cnt
+
+
+def test_autotune_keeps_bits():
+    """The autotuner only changes speed: its pick gives the oracle's bits."""
+    from paper_1702_03657_gb300.tune import autotune
+    wl = W.batched(4, ntexts=300, n_patterns=3000)
+    t = pm.pm_build(wl.patterns)
+    tx = dev(wl.text)
+    off = dev(wl.offsets.astype(np.int64))
+    res = autotune(t, tx, off, reps=2)
+    assert res["tried"] >= 4
+    assert pm.pm_get_config(t) == res["config"]
+    o_ids, o_counts, _ = oracle.Trie(wl.patterns).scan_batch(wl.text, wl.offsets)
+    ids, counts = batch_gpu(t, wl)
+    assert np.array_equal(ids, o_ids) and np.array_equal(counts, o_counts)
