@@ -47,6 +47,8 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--serving-requests", type=int, default=10000)
     ap.add_argument("--text-mib", type=int, default=256,
                     help="text size (the metric is quoted at 256; smaller sizes "
                          "are for profiler captures)")
@@ -243,6 +245,79 @@ def bench_batched(pm, W, torch, reps: int):
             "tuned_config": tuned["config"], "configs_tried": tuned["tried"]}
 
 
+def bench_serving(pm, W, torch, n_req: int, loads=(0.1, 0.25, 0.5, 0.75, 0.9)):
+    """Serving config: 50,000 byte patterns (6-64 B); requests 90 % U[40,1500]
+    B and 10 % log-uniform [1,16] MiB of uniform bytes with plants at 1 per
+    2 KiB, arriving as a Poisson process. Each request's text is a slice of
+    one pinned pool (so the trace needs no per-request host buffers). The
+    continuous-batching server and plain per-request launches replay the same
+    traces natively; latency = completion seen on the host - scheduled
+    arrival."""
+    pats = W.serving_patterns(0)
+    trie = pm.pm_build(pats)
+    rng = np.random.Generator(np.random.MT19937(7))
+    large = rng.random(n_req) < 0.1
+    sizes = np.where(large,
+                     np.exp(rng.uniform(np.log(1 << 20), np.log(16 << 20), n_req)).astype(np.int64),
+                     rng.integers(40, 1501, n_req))
+    pool_n = (96 << 20)
+    pool = rng.integers(0, 256, size=pool_n, dtype=np.uint8)
+    W._plant_bernoulli(rng, pool, pats, 1.0 / 2048)
+    pool_t = torch.from_numpy(pool).pin_memory()
+    starts = rng.integers(0, pool_n - sizes + 1)
+    h_ptrs = [pool_t.data_ptr() + int(o) for o in starts]
+    lens = [int(x) for x in sizes]
+    total = int(sizes.sum())
+    out_off = np.concatenate([[0], np.cumsum(sizes)])
+    ids_s = torch.empty(total, dtype=torch.int32, device="cuda")
+    ids_p = torch.empty(total, dtype=torch.int32, device="cuda")
+    cnt_s = torch.empty(n_req, dtype=torch.int64, device="cuda")
+    cnt_p = torch.empty(n_req, dtype=torch.int64, device="cuda")
+    dtx = torch.empty(total, dtype=torch.uint8, device="cuda")
+    ip_s = [ids_s.data_ptr() + 4 * int(o) for o in out_off[:-1]]
+    ip_p = [ids_p.data_ptr() + 4 * int(o) for o in out_off[:-1]]
+    cp_s = [cnt_s.data_ptr() + 8 * i for i in range(n_req)]
+    cp_p = [cnt_p.data_ptr() + 8 * i for i in range(n_req)]
+    tp = [dtx.data_ptr() + int(o) for o in out_off[:-1]]
+    srv = pm.pm_server_create(trie)
+
+    def gbps(nbytes, ns):
+        return 8.0 * nbytes / max(ns, 1)
+
+    def run(arr):
+        lat_s, wall_s = pm.pm_server_replay(srv, h_ptrs, lens, arr, ip_s, cp_s)
+        lat_p, wall_p = pm.pm_replay_plain(trie, h_ptrs, lens, arr, tp, ip_p, cp_p)
+        torch.cuda.synchronize()
+        q = lambda lat, p_: round(float(np.percentile(lat, p_)) / 1e6, 4)
+        return {"server": {"gbps": round(gbps(total, wall_s), 2), "p50_ms": q(lat_s, 50),
+                           "p99_ms": q(lat_s, 99)},
+                "plain": {"gbps": round(gbps(total, wall_p), 2), "p50_ms": q(lat_p, 50),
+                          "p99_ms": q(lat_p, 99)}}
+
+    zero = np.zeros(n_req, dtype=np.uint64)
+    run(zero)                                   # warm-up
+    sat = run(zero)                             # everything arrives at once
+    max_gbps = sat["server"]["gbps"]
+    mean_bytes = total / n_req
+    points = []
+    for f in loads:
+        rate = f * max_gbps * 1e9 / 8 / mean_bytes          # requests per second
+        arr = (W.poisson_arrivals(11, n_req, rate) * 1e9).astype(np.uint64)
+        r = run(arr)
+        r["offered_gbps"] = round(f * max_gbps, 2)
+        r["load"] = f
+        points.append(r)
+    mism = int((ids_s != ids_p).sum().item()) + int((cnt_s != cnt_p).sum().item())
+    st = pm.pm_server_get_stats(srv)
+    pm.pm_server_destroy(srv)
+    return {"workload": f"{n_req} requests, {total} bytes, 90 % U[40,1500] B / 10 % "
+                        f"log-uniform [1,16] MiB, 50,000 patterns of 6-64 B, Poisson arrivals",
+            "saturation": sat, "max_served_gbps": max_gbps, "points": points,
+            "mismatches_server_vs_plain": mism,
+            "server_stats": {k: st[k] for k in ("batches", "max_batch_seen",
+                                                "max_inflight_seen", "admission_waits")}}
+
+
 def run_reference(args, rank, world):
     """CPU oracle arm: rank 0 only; each step a bounded sample."""
     if rank != 0:
@@ -384,6 +459,7 @@ def main():
     if not args.no_cpu_baseline and world == 1:
         cpu = cpu_baseline(wl, args.cpu_seconds)
     batched = None if args.no_batched else bench_batched(pm, W, torch, reps=200)
+    serving = None if args.no_serving else bench_serving(pm, W, torch, args.serving_requests)
     line = {
         "metric": METRIC, "value": round(gbps, 2), "unit": "Gbps", "n_gpus": world,
         "steps": K, "warmup": args.warmup, "ms_per_step": round(total_ms / K, 5),
@@ -410,6 +486,7 @@ def main():
                                        "dense_k_max")},
         "matches": count,
         "batched": batched,
+        "serving": serving,
     }
     print(json.dumps(line), flush=True)
     if world > 1:

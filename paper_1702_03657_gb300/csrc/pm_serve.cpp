@@ -177,10 +177,20 @@ bool issue_batch(pm_server *s, Slot &sl, size_t n, uint64_t bytes, uint64_t aoff
     uint64_t o = 0;
     size_t t = 0;
     sl.reqs.clear();
+    // classify once: small requests while the staging buffer has room
+    std::vector<char> small_req(n, 0);
+    uint64_t staged = 0;
+    for (size_t i = 0; i < n; ++i) {
+        const uint64_t L = s->pending[i].len;
+        if (L <= kSmallReq && staged + L <= kStageBytes) {
+            small_req[i] = 1;
+            staged += L;
+        }
+    }
     for (int pass = 0; pass < 2; ++pass) {
         for (size_t i = 0; i < n; ++i) {
             const Req &r = s->pending[i];
-            const bool small = r.len <= kSmallReq && o + r.len <= kStageBytes;
+            const bool small = small_req[i] != 0;
             if ((pass == 0) != small) continue;
             if (small) {
                 if (r.len) std::memcpy(sl.h_stage + o, r.h_text, r.len);
@@ -199,6 +209,7 @@ bool issue_batch(pm_server *s, Slot &sl, size_t n, uint64_t bytes, uint64_t aoff
             cudaMemcpyAsync(s->d_arena + aoff, sl.h_stage, o, cudaMemcpyHostToDevice, st) != cudaSuccess)
             return false;
     }
+    if (t != n || o != bytes) return false;  // every request placed exactly once
     sl.h_off[n] = o;
     if (cudaMemcpyAsync(sl.d_off, sl.h_off, 8 * (n + 1), cudaMemcpyHostToDevice, st) != cudaSuccess ||
         cudaMemcpyAsync(sl.d_ids, sl.h_ids, sizeof(void *) * n, cudaMemcpyHostToDevice, st) != cudaSuccess ||

@@ -142,6 +142,34 @@ def test_replay_server_and_plain(setup):
             assert np.array_equal(ids[i][:len(text)].cpu().numpy(), exp_ids)
 
 
+def test_mixed_small_and_large_in_one_batch(setup):
+    """Many small requests and several large ones submitted at once land in
+    shared batches (small ones gathered through the staging buffer, large
+    ones copied directly); every id and count must match the scan alone."""
+    pats, reqs, trie = setup
+    rng = np.random.Generator(np.random.MT19937(21))
+    pool = rng.integers(0, 256, size=24 << 20, dtype=np.uint8)
+    W._plant_bernoulli(rng, pool, pats, 1.0 / 1024)
+    sizes = [int(x) for x in rng.integers(40, 1500, 400)] + [(2 << 20) + 7, (5 << 20) + 1,
+                                                              70 << 10, 3 << 20]
+    rng.shuffle(sizes)
+    starts = [int(rng.integers(0, len(pool) - z)) for z in sizes]
+    texts = [pool[a:a + z] for a, z in zip(starts, sizes)]
+    ids, cnt = outputs(texts)
+    srv = pm.pm_server_create(trie, max_inflight=1, max_batch=4096,
+                              max_batch_bytes=64 << 20)
+    rids = [pm.pm_submit(srv, t, ids[i], cnt[i]) for i, t in enumerate(texts)]
+    for r in rids:
+        pm.pm_wait(srv, r, 20000)
+    st = pm.pm_server_get_stats(srv)
+    pm.pm_server_destroy(srv)
+    assert st["completed"] == len(texts) and st["max_batch_seen"] > 8
+    for i, text in enumerate(texts):
+        exp_ids, exp_cnt = alone(trie, text)
+        assert int(cnt[i].item()) == exp_cnt, i
+        assert np.array_equal(ids[i][:len(text)].cpu().numpy(), exp_ids), i
+
+
 def test_server_errors(setup):
     pats, reqs, trie = setup
     host = pm.pm_build_host([b"abc"])
