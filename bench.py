@@ -55,13 +55,6 @@ def parse():
     return ap.parse_args()
 
 
-def dist_env():
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return rank, world, local
-
-
 # ----------------------------------------------------------------------------
 # clocks during the timed region
 
@@ -358,6 +351,7 @@ def run_reference(args, rank, world):
 
 def main():
     args = parse()
+    from paper_1702_03657_gb300.dist import dist_env, max_over_ranks
     rank, world, local = dist_env()
     if args.impl == "reference":
         run_reference(args, rank, world)
@@ -414,10 +408,7 @@ def main():
     clocks.stop()
     step_ms = [ev[i].elapsed_time(ev[i + 1]) for i in range(K)]
     total_ms = ev[0].elapsed_time(ev[K])
-    if world > 1:
-        tt = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        total_ms = float(tt.item())
+    total_ms = max_over_ranks(total_ms, "cuda")
     count = int(cnt.item())
 
     gbps = 8.0 * n * world * K / (total_ms / 1e3) / 1e9
@@ -438,10 +429,7 @@ def main():
     for _ in range(args.e2e_steps):
         hc = pm.pm_scan_host(trie, hn, hi)
     e2e_s = max(time.perf_counter() - t0, 1e-9)
-    if world > 1:
-        tt = torch.tensor([e2e_s], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e_s = float(tt.item())
+    e2e_s = max_over_ranks(e2e_s, "cuda")
     chunk = 32 << 20
     nchunks = (n + chunk - 1) // chunk
     h2d = n + (nchunks - 1) * (stats["max_len"] - 1)
