@@ -86,8 +86,10 @@ typedef struct {
     uint64_t device_bytes;   /* everything the handle holds on the device      */
 } pm_trie_stats;
 
-/* Launch configuration of the scan kernel (picked by an autotuner). Every
- * warp of a CTA is an independent pipeline over its own text tiles. */
+/* Launch configuration of the scan kernel (picked by an autotuner). The
+ * producer warps of a CTA are independent pipelines over their own text
+ * tiles; they queue the positions that need a trie walk in a shared ring
+ * that the walker warps drain. */
 typedef struct {
     int32_t threads;      /* threads per CTA: 128, 256, 512 or 1024           */
     int32_t tile;         /* text bytes per warp tile: multiple of 128,       */
@@ -97,8 +99,10 @@ typedef struct {
     int32_t filter_bits;  /* child-filter width per k-gram: 8, 16 or 32       */
     int32_t row_search;   /* 0: linear, 1: binary search of the byte column   */
     int32_t ctas_per_sm;  /* persistent grid = SMs * ctas_per_sm (0: maximum) */
-    int32_t stages;       /* tiles in flight per warp (TMA), 2..4             */
+    int32_t stages;       /* tiles in flight per producer warp (TMA), 2..4    */
     int32_t checked;      /* 1: bounds-checked scan (PM_ERR_BOUNDS on error)  */
+    int32_t walkers;      /* warps per CTA that run the CRS walks the others  */
+                          /* queue, 1 .. threads/32 - 1                       */
 } pm_config;
 
 /* ---- trie construction (Section III, steps I, II, VI and the CRS step) --

@@ -70,9 +70,11 @@ int32_t pick_bits(const pm_trie *h, int32_t k)
     return 0;
 }
 
-// Default launch configuration: as many independent warps as fit (up to 32
-// per CTA, one CTA per SM) with 1-2 KiB warp tiles double-buffered, at the
-// deepest filter level that fits; an autotuner may refine it.
+// Default launch configuration: one 1024-thread CTA per SM (26 producer and
+// 6 walker warps), 1-2 KiB producer tiles double-buffered, the deepest
+// filter level that fits; for the byte alphabet's Bloom filter the wider
+// filter with smaller tiles comes first (fewer walks). An autotuner may
+// refine it.
 pm_config default_config(const pm_trie *h, int smem_limit)
 {
     pm_config c{};
@@ -81,14 +83,23 @@ pm_config default_config(const pm_trie *h, int smem_limit)
     c.stages = 2;
     c.checked = 0;
     const uint64_t limit = (uint64_t)smem_limit - 1024;
+    struct Pref {
+        int32_t bits, tile;
+    };
     for (int32_t k = (int32_t)h->host.dense_k_max; k >= 0; --k) {
         c.dense_k = k;
-        c.filter_bits = pick_bits(h, k);
-        if (!c.filter_bits) continue;
+        const bool bloom = h->host.C == 256 && k >= 2;
+        std::vector<Pref> prefs;
+        if (bloom) prefs = {{16, 1024}, {8, 2048}, {8, 1536}, {8, 1024}};
+        const int32_t exact = pick_bits(h, k);
+        for (int32_t tile : {2048, 1536, 1024, 512, 256, 128}) prefs.push_back({exact, tile});
         for (int32_t threads : {1024, 512, 256, 128}) {
-            for (int32_t tile : {2048, 1536, 1024, 512, 256, 128}) {
+            for (const Pref &pf : prefs) {
+                if (!have_filter(h, k, pf.bits)) continue;
                 c.threads = threads;
-                c.tile = tile;
+                c.tile = pf.tile;
+                c.filter_bits = pf.bits;
+                c.walkers = std::max<int32_t>(1, threads / 32 * 3 / 16);
                 if (pm::scan_smem_bytes(h->dev, c) <= limit) return c;
             }
         }
@@ -97,6 +108,7 @@ pm_config default_config(const pm_trie *h, int smem_limit)
     c.filter_bits = 8;
     c.threads = 128;
     c.tile = 128;
+    c.walkers = 1;
     return c;
 }
 
@@ -124,6 +136,10 @@ int validate_config(const pm_trie *h, const pm_config &c, std::string &why)
     }
     if (c.ctas_per_sm < 0 || c.ctas_per_sm > 32) {
         why = "ctas_per_sm must be 0..32";
+        return PM_ERR_INVAL;
+    }
+    if (c.walkers < 1 || c.walkers >= c.threads / 32) {
+        why = "walkers must be in 1 .. threads/32 - 1";
         return PM_ERR_INVAL;
     }
     if (c.row_search < 0 || c.row_search > 1 || c.checked < 0 || c.checked > 1) {

@@ -67,14 +67,16 @@ struct KParams {
     uint32_t lw;                // log2 W
     uint32_t binary;
     uint32_t stages;
+    uint32_t walkers;           // walker warps per CTA (the rest produce)
     uint32_t aligned;
     uint32_t ids_aligned;
     // shared-memory layout (byte offsets)
-    uint32_t off_dense, off_lut, off_warp;  // shared tables, then per-warp blocks
-    uint32_t warp_bytes;          // bytes of one warp's block
-    uint32_t off_queue, off_stages;  // inside a warp's block (after its mbarriers)
+    uint32_t off_dense, off_lut, off_ring, off_warp;  // shared tables and ring, then per-warp blocks
+    uint32_t warp_bytes;          // bytes of one producer warp's block
+    uint32_t off_stages;          // inside a warp's block (after its mbarriers)
     uint32_t stage_bytes;         // tile + halo
-    uint32_t filt_u4, dense_u4;   // table sizes in 16-byte units
+    uint32_t filt_u4;             // filter size in 16-byte units
+    uint32_t dense_u4;            // dense table size in 16-byte units (0: none)
     uint32_t filt_words;          // filter size in u32 words
 };
 
@@ -214,20 +216,38 @@ __device__ __forceinline__ uint32_t find_text(const uint64_t *off, uint32_t ntex
     return lo;
 }
 
-// Per-warp walk queue of 4-position groups. Entry x = tile-relative position
-// of the group | positions to walk << 16 | of those, positions walked from
-// the root << 20; y = the warp's tile sequence number. Walks read the text
-// from global memory, so queued groups outlive their tile's staging buffer
-// and are walked in rounds of at least one group per lane.
-constexpr uint32_t kQueue = 64;    // >= 31 pending + 32 from one warp step
-constexpr uint32_t kRound = 32;    // groups that trigger a round
+// Walk ring, in shared memory, between the producer warps (tiles, filter)
+// and the walker warps (CRS walks). An entry is one 4-position group with at
+// least one position to walk: x = position of the group (low 32 bits), y =
+// its high 24 bits | positions to walk << 24 | of those, positions walked
+// from the root << 28, z, w = the group's text bytes [pos, pos+8).
+// Each cell carries a sequence number (a bounded multi-producer,
+// multi-consumer ring): cell i starts at i; the producer of slot s waits for
+// s, fills the cell and sets s+1; the walker of slot s waits for s+1, takes
+// the entry and sets s+kRing, freeing the cell for slot s+kRing only.
+constexpr uint32_t kRing = 512;  // entries (power of two)
+
+struct Ring {
+    unsigned int wr;        // slots reserved by producers
+    unsigned int rd;        // slots taken by walkers
+    unsigned int pdone;     // producer warps finished
+    unsigned int progress;  // tiles finished by producers (walkers' heartbeat)
+};
+
+// Bounded spin: true while the budget lasts (a few seconds of SM clocks).
+__device__ __forceinline__ bool spin_ok(long long t0)
+{
+    return clock64() - t0 < kWaitBudget;
+}
 
 // Walk the CRS rows from node v with the text byte at j until the first
-// mismatch or the text end (Section II-C). The byte and the row bounds are
-// fetched together; the first column entry and its next state too. Returns
-// the deepest node; j is advanced past the matched bytes.
+// mismatch or the text end (Section II-C). Bytes [wpos, wpos+8) come from
+// the group's window; later ones from global memory. The byte and the row
+// bounds are fetched together, then the first column entry and its next
+// state. Returns the deepest node; j is advanced past the matched bytes.
 template <int MODE>
 __device__ __forceinline__ uint32_t crs_walk(const TrieDev &t, const uint8_t *text,
+                                             unsigned long long wpos, unsigned long long win,
                                              unsigned long long &j, unsigned long long tend,
                                              uint32_t v, uint32_t binary, unsigned long long &look)
 {
@@ -237,7 +257,8 @@ __device__ __forceinline__ uint32_t crs_walk(const TrieDev &t, const uint8_t *te
             record_error(PM_ERR_BOUNDS);
             break;
         }
-        const uint32_t b = __ldg(text + j);
+        const unsigned long long d = j - wpos;
+        const uint32_t b = d < 8 ? (uint32_t)(win >> (8 * d)) & 0xFFu : (uint32_t)__ldg(text + j);
         const uint32_t r0 = ld_trie_u32(t.row_ptr + v, pol), r1 = ld_trie_u32(t.row_ptr + v + 1, pol);
         if (MODE == MODE_CHECKED && (r1 < r0 || r1 > t.nnz)) {
             record_error(PM_ERR_BOUNDS);
@@ -295,71 +316,148 @@ __device__ __forceinline__ uint32_t class_of(const uint32_t *s_lut, uint32_t lan
     return (s_lut[(b >> 2) * 32 + lane] >> ((b & 3) * 8)) & 0xFFu;
 }
 
-// Phase 2: every lane takes queued groups and walks their flagged positions,
-// each from its depth-k node (k-gram code from the text, node from the dense
-// table; a k-gram that is not a root path stops the walk above depth k,
-// without a match) or from the root. A walk that finds a match patches its
-// position's id and adds its count.
+// One lane walks the flagged positions of a ring entry: each from its
+// depth-k node (k-gram code from the window, node from the dense table; a
+// k-gram that is not a root path stops the walk above depth k, without a
+// match) or from the root. A walk that finds a match patches its position's
+// id and adds its count.
 template <bool IDENT, bool BATCH, int MODE>
-__device__ __forceinline__ void walk_queue(const KParams &p, const uint2 *queue, uint32_t qn,
-                                           unsigned long long gw, unsigned long long TW,
-                                           unsigned long long end, uint32_t k,
-                                           const uint32_t *s_lut, uint32_t lane,
-                                           unsigned long long &acc, unsigned long long &look)
+__device__ __forceinline__ void walk_group(const KParams &p, uint4 e, unsigned long long end,
+                                           uint32_t k, const uint32_t *s_lut, const uint2 *s_dense,
+                                           uint32_t lane, unsigned long long &acc,
+                                           unsigned long long &look)
 {
     const TrieDev &t = p.t;
-    __syncwarp();
-    for (uint32_t i = lane; i < qn; i += 32) {
-        const uint2 e = queue[i];
-        const unsigned long long g0 = (gw + e.y * TW) * p.tile + (e.x & 0xFFFFu);
-        uint32_t m = (e.x >> 16) & 0xFu;
-        const uint32_t rootm = e.x >> 20;
-        unsigned long long tend = end;
-        uint32_t txt = 0;
+    const unsigned long long g0 = ((unsigned long long)(e.y & 0xFFFFFFu) << 32) | e.x;
+    const unsigned long long win = ((unsigned long long)e.w << 32) | e.z;
+    uint32_t m = (e.y >> 24) & 0xFu;
+    const uint32_t rootm = e.y >> 28;
+    unsigned long long tend = end;
+    uint32_t txt = 0;
+    if (BATCH) {
+        txt = find_text(p.offsets, p.ntexts, g0 + (__ffs(m) - 1));
+        tend = __ldg(p.offsets + txt + 1);
+    }
+    while (m) {
+        const uint32_t q = __ffs(m) - 1;
+        m &= m - 1;
+        const unsigned long long pos = g0 + q;
         if (BATCH) {
-            txt = find_text(p.offsets, p.ntexts, g0 + (__ffs(m) - 1));
-            tend = __ldg(p.offsets + txt + 1);
+            while (pos >= tend) {
+                ++txt;
+                tend = __ldg(p.offsets + txt + 1);
+            }
         }
-        while (m) {
-            const uint32_t q = __ffs(m) - 1;
-            m &= m - 1;
-            const unsigned long long pos = g0 + q;
-            if (BATCH) {
-                while (pos >= tend) {
-                    ++txt;
-                    tend = __ldg(p.offsets + txt + 1);
-                }
+        uint32_t v = 0;
+        unsigned long long j = pos;
+        if (!((rootm >> q) & 1u) && k > 0) {
+            uint32_t code = 0;
+            for (uint32_t j2 = 0; j2 < k; ++j2) {
+                const uint32_t d = q + j2;
+                const uint32_t b = d < 8 ? (uint32_t)(win >> (8 * d)) & 0xFFu : (uint32_t)__ldg(p.text + pos + j2);
+                code = code * t.C + class_of<IDENT>(s_lut, lane, b);
             }
-            uint32_t v = 0;
-            unsigned long long j = pos;
-            if (!((rootm >> q) & 1u) && k > 0) {
-                uint32_t code = 0;
-                for (uint32_t j2 = 0; j2 < k; ++j2)
-                    code = code * t.C + class_of<IDENT>(s_lut, lane, __ldg(p.text + pos + j2));
-                const uint2 d = __ldg(p.dense + (code >> 5));
-                const uint32_t bit = code & 31u;
-                if (!((d.x >> bit) & 1u)) continue;
-                v = p.first_k + d.y + __popc(d.x & ((1u << bit) - 1u));
-                j = pos + k;
+            if (MODE == MODE_CHECKED && (code >> 5) >= p.dense_u4 * 2) {
+                record_error(PM_ERR_BOUNDS);
+                continue;
             }
-            v = crs_walk<MODE>(t, p.text, j, tend, v, p.binary, look);
-            if (j - pos >= t.min_len) {
-                const int2 em = __ldg(t.emit + v);
-                if (em.y) {
-                    if (BATCH && p.out_ids)
-                        p.out_ids[txt][pos - __ldg(p.offsets + txt)] = em.x;
-                    else
-                        p.ids[pos] = em.x;
-                    if (BATCH)
-                        atomicAdd(reinterpret_cast<unsigned long long *>(p.counts + txt),
-                                  (unsigned long long)em.y);
-                    else
-                        acc += (unsigned)em.y;
-                }
+            const uint2 d = s_dense[code >> 5];
+            const uint32_t bit = code & 31u;
+            if (!((d.x >> bit) & 1u)) continue;
+            v = p.first_k + d.y + __popc(d.x & ((1u << bit) - 1u));
+            j = pos + k;
+        }
+        v = crs_walk<MODE>(t, p.text, g0, win, j, tend, v, p.binary, look);
+        if (j - pos >= t.min_len) {
+            const int2 em = __ldg(t.emit + v);
+            if (em.y) {
+                if (BATCH && p.out_ids)
+                    p.out_ids[txt][pos - __ldg(p.offsets + txt)] = em.x;
+                else
+                    p.ids[pos] = em.x;
+                if (BATCH)
+                    atomicAdd(reinterpret_cast<unsigned long long *>(p.counts + txt),
+                              (unsigned long long)em.y);
+                else
+                    acc += (unsigned)em.y;
             }
         }
     }
-    __syncwarp();
+}
+
+// Walker warp: takes up to 32 ring entries at a time, one per lane, until
+// every producer warp has finished and the ring is empty.
+template <bool IDENT, bool BATCH, int MODE>
+__device__ __forceinline__ void walker_loop(const KParams &p, Ring *ring, const uint4 *entries,
+                                            unsigned int *flags, uint32_t NP,
+                                            unsigned long long end, uint32_t k,
+                                            const uint32_t *s_lut, const uint2 *s_dense,
+                                            uint32_t lane, unsigned long long &acc,
+                                            unsigned long long &look)
+{
+    volatile Ring *vr = ring;
+    volatile unsigned int *vf = flags;
+    // the idle wait is bounded, counted from the producers' last progress
+    long long t0 = clock64();
+    uint32_t seen = vr->progress;
+    while (true) {
+        uint32_t base = 0, take = 0;  // take 0xFFFFFFFF: stop
+        if (lane == 0) {
+            while (true) {
+                const uint32_t rd = vr->rd, wr = vr->wr;
+                if ((int32_t)(wr - rd) > 0) {
+                    const uint32_t n = min(32u, wr - rd);
+                    if (atomicCAS(&ring->rd, rd, rd + n) == rd) {
+                        base = rd;
+                        take = n;
+                        break;
+                    }
+                    continue;
+                }
+                if (vr->pdone >= NP) {
+                    __threadfence_block();
+                    if ((int32_t)(vr->wr - vr->rd) <= 0) {
+                        take = 0xFFFFFFFFu;
+                        break;
+                    }
+                    continue;
+                }
+                const uint32_t now = vr->progress;
+                if (now != seen) {
+                    seen = now;
+                    t0 = clock64();
+                } else if (!spin_ok(t0)) {
+                    record_error(PM_ERR_TIMEOUT);
+                    take = 0xFFFFFFFFu;
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        take = __shfl_sync(0xffffffffu, take, 0);
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (take == 0xFFFFFFFFu) break;
+        if (lane < take) {
+            const uint32_t slot = base + lane, idx = slot & (kRing - 1);
+            const long long w0 = clock64();
+            bool ok = true;
+            while (vf[idx] != slot + 1u) {  // until the producer has filled it
+                if (clock64() - w0 > kWaitBudget) {
+                    record_error(PM_ERR_TIMEOUT);
+                    ok = false;
+                    break;
+                }
+            }
+            if (ok) {
+                __threadfence_block();
+                const uint4 e = entries[idx];
+                __threadfence_block();
+                vf[idx] = slot + kRing;  // free for the slot one lap later
+                walk_group<IDENT, BATCH, MODE>(p, e, end, k, s_lut, s_dense, lane, acc, look);
+            }
+        }
+        __syncwarp();
+    }
 }
 
 // KF: the filter level k when fixed at compile time (byte alphabet), or -1
@@ -372,20 +470,28 @@ __global__ void __launch_bounds__(1024, 1) pfac_scan_kernel(const KParams p)
     const TrieDev &t = p.t;
     const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const uint32_t NW = blockDim.x >> 5;
+    const uint32_t NP = NW - p.walkers;  // producer warps; the rest walk
 
     const unsigned long long total = BATCH ? __ldg(p.offsets + p.ntexts) : p.total;
     const unsigned long long end = BATCH ? total : p.limit;
     const unsigned long long ntiles = (total + p.tile - 1) / p.tile;
-    if ((unsigned long long)blockIdx.x * NW >= ntiles) return;
+    if ((unsigned long long)blockIdx.x * NP >= ntiles) return;
 
     uint32_t *s_filt = reinterpret_cast<uint32_t *>(smem);
+    uint2 *s_dense = reinterpret_cast<uint2 *>(smem + p.off_dense);
     uint32_t *s_lut = reinterpret_cast<uint32_t *>(smem + p.off_lut);
+    uint4 *entries = reinterpret_cast<uint4 *>(smem + p.off_ring);
+    unsigned int *flags = reinterpret_cast<unsigned int *>(smem + p.off_ring + kRing * 16);
+    Ring *ring = reinterpret_cast<Ring *>(smem + p.off_ring + kRing * 20);
 
     // Tables into shared memory, shared by all warps of the CTA.
     {
         const uint4 *src = reinterpret_cast<const uint4 *>(p.filter);
         uint4 *dst = reinterpret_cast<uint4 *>(s_filt);
         for (uint32_t i = tid; i < p.filt_u4; i += blockDim.x) dst[i] = __ldg(src + i);
+        const uint4 *dsrc = reinterpret_cast<const uint4 *>(p.dense);
+        uint4 *ddst = reinterpret_cast<uint4 *>(s_dense);
+        for (uint32_t i = tid; i < p.dense_u4; i += blockDim.x) ddst[i] = __ldg(dsrc + i);
         if (!IDENT) {
             // class LUT replicated per lane: word (b/4)*32 + lane holds the
             // classes of bytes 4*(b/4) .. +3, so lane l always hits bank l.
@@ -396,257 +502,300 @@ __global__ void __launch_bounds__(1024, 1) pfac_scan_kernel(const KParams p)
                            ((uint32_t)__ldg(t.cls + 4 * w + 3) << 24);
             }
         }
+        for (uint32_t i = tid; i < kRing; i += blockDim.x) flags[i] = i;  // cell i free for slot i
+        if (tid == 0) *ring = Ring{0u, 0u, 0u, 0u};
     }
     __syncthreads();  // the only CTA-wide barrier: warps run independently below
-
-    const unsigned long long gw = (unsigned long long)blockIdx.x * NW + warp;
-    const unsigned long long TW = (unsigned long long)gridDim.x * NW;
-    if (gw >= ntiles) return;
-    const unsigned long long my_tiles = (ntiles - 1 - gw) / TW + 1;
-
-    uint8_t *wsm = smem + p.off_warp + (size_t)warp * p.warp_bytes;
-    uint64_t *bars = reinterpret_cast<uint64_t *>(wsm);
-    uint2 *queue = reinterpret_cast<uint2 *>(wsm + p.off_queue);
-    uint8_t *stages = wsm + p.off_stages;
-
-    const unsigned long long tstride = TW * p.tile;  // text between a warp's tiles
-    if (lane == 0) {
-        for (uint32_t s = 0; s < p.stages; ++s) mbar_init(&bars[s], 1);
-        fence_mbar_init();
-        const unsigned long long pre = my_tiles < p.stages ? my_tiles : p.stages;
-        for (unsigned long long i = 0; i < pre; ++i)
-            issue_tile(p, stages, bars, (uint32_t)i, (gw + i * TW) * p.tile, end);
-    }
-    __syncwarp();
 
     constexpr uint32_t KFU = KF > 0 ? (uint32_t)KF : 0u;  // KF as unsigned (0 if runtime)
     const uint32_t k = KF >= 0 ? KFU : p.k;
     const uint32_t gram = p.gram;
-    const uint32_t C = t.C;
-    const uint32_t lw = p.lw;
-    const uint32_t wmask = (1u << lw) - 1u;
-    // IDENT: filter bit index = low 8k+lw bits of the little-endian window
-    const uint32_t imask = KF >= 0 ? (uint32_t)((1ull << (8 * (KF >= 0 ? KF : 0) + lw)) - 1ull) : 0u;
     unsigned long long acc = 0;   // matches (single text)
     unsigned long long look = 0;  // lookups (MODE_LOOKUPS)
-    uint32_t qn = 0;              // warp-uniform queue length
 
-    uint32_t s = 0, phase = 0;            // stage and its mbarrier phase
-    unsigned long long t0 = gw * p.tile;  // start of the current tile
-    const unsigned long long ahead = (unsigned long long)p.stages * tstride;
-    for (unsigned long long it = 0; it < my_tiles; ++it, t0 += tstride) {
-        const uint32_t nbytes = (uint32_t)tile_bytes(p, t0, end);
-        uint8_t *st = stages + (size_t)s * p.stage_bytes;
+    if (warp >= NP) {
+        walker_loop<IDENT, BATCH, MODE>(p, ring, entries, flags, NP, end, k, s_lut, s_dense, lane,
+                                        acc, look);
+    } else {
+        const unsigned long long gw = (unsigned long long)blockIdx.x * NP + warp;
+        const unsigned long long TW = (unsigned long long)gridDim.x * NP;
+        const unsigned long long my_tiles = gw < ntiles ? (ntiles - 1 - gw) / TW + 1 : 0;
 
-        const bool ok = __all_sync(0xffffffffu, mbar_wait_bounded(&bars[s], phase));
-        if (!ok) {
-            if (lane == 0) {
-                record_error(PM_ERR_TIMEOUT);
-                // copies still in flight: tiles it .. it+stages-1
-                for (unsigned long long j = 0; j < p.stages && it + j < my_tiles; ++j) {
-                    const uint32_t sj = (uint32_t)((s + j) % p.stages);
-                    mbar_wait_bounded(&bars[sj], phase ^ (uint32_t)((s + j) >= p.stages));
-                }
-            }
-            return;
+        uint8_t *wsm = smem + p.off_warp + (size_t)warp * p.warp_bytes;
+        uint64_t *bars = reinterpret_cast<uint64_t *>(wsm);
+        uint8_t *stages = wsm + p.off_stages;
+        volatile unsigned int *vf = flags;
+
+        const unsigned long long tstride = TW * p.tile;  // text between a warp's tiles
+        if (lane == 0 && my_tiles) {
+            for (uint32_t s = 0; s < p.stages; ++s) mbar_init(&bars[s], 1);
+            fence_mbar_init();
+            const unsigned long long pre = my_tiles < p.stages ? my_tiles : p.stages;
+            for (unsigned long long i = 0; i < pre; ++i)
+                issue_tile(p, stages, bars, (uint32_t)i, (gw + i * TW) * p.tile, end);
         }
-        const uint32_t nb16 = p.aligned ? (nbytes & ~15u) : 0u;
-        if (nb16 < nbytes) {
-            for (uint32_t i = nb16 + lane; i < nbytes; i += 32) st[i] = __ldg(p.text + t0 + i);
-            __syncwarp();
-        }
+        __syncwarp();
 
-        const uint32_t tile_n = (uint32_t)(total - t0 < p.tile ? total - t0 : p.tile);
-        uint32_t cur = 0;
-        unsigned long long text_end = end;
-        if (BATCH) {
-            cur = find_text(p.offsets, p.ntexts, t0 + 4 * lane < total ? t0 + 4 * lane : t0);
-            text_end = __ldg(p.offsets + cur + 1);
-        }
-        uint32_t rel_end = rel_end_of(text_end, t0);
-        // groups [lp0, lp0+4) with lp0 + 4 <= fast_n take the fast path
-        auto fast_bound = [&]() -> uint32_t {
-            const uint32_t r = rel_end >= gram - 1 ? rel_end - (gram - 1) : 0u;
-            return r < tile_n ? r : tile_n;
-        };
-        uint32_t fast_n = fast_bound();
-        int32_t *idt = p.ids + t0;  // this tile's ids
+        const uint32_t C = t.C;
+        const uint32_t lw = p.lw;
+        const uint32_t wmask = (1u << lw) - 1u;
+        // IDENT: filter bit index = low 8k+lw bits of the little-endian window
+        const uint32_t imask = KF >= 0 ? (uint32_t)((1ull << (8 * KFU + lw)) - 1ull) : 0u;
+        bool failed = false;
 
-        const uint32_t iters = (tile_n + 127) >> 7;
-        for (uint32_t i = 0; i < iters; ++i) {
-            const uint32_t lp0 = (i << 7) + 4 * lane;
-            const uint32_t *wp = reinterpret_cast<const uint32_t *>(st + lp0);
-            if (BATCH && lp0 < tile_n && t0 + lp0 >= text_end) {
-                while (t0 + lp0 >= text_end) {
-                    ++cur;
-                    text_end = __ldg(p.offsets + cur + 1);
-                }
-                rel_end = rel_end_of(text_end, t0);
-                fast_n = fast_bound();
-            }
-            const uint32_t cur0 = cur;  // text of position lp0
-            uint32_t need = 0;   // bit q: position lp0+q passed the filter
-            uint32_t rootm = 0;  // bit q: position lp0+q is walked from the root
-            if (MODE != MODE_LOOKUPS && lp0 + 4 <= fast_n) {
-                // Phase 1 fast path: four positions, all bytes up to
-                // lp0+3+k inside the text. The filter decides, in shared
-                // memory, which positions can reach depth k+1.
-                if (IDENT && KF >= (int)kBloomK) {
-                    // blocked Bloom test of the (k+1)-gram at each position
-                    const uint32_t w0 = wp[0], w1 = wp[1];
-                    const uint32_t sh = 32u - (8u * KFU + lw - 5u);
-                    const uint32_t gsh = G > 0 ? 32u - 8u * G : 32u - 8u * gram;
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        const uint32_t win = q == 0 ? w0 : __funnelshift_r(w0, w1, 8 * q);
-                        // bytes q .. q+g-1, shifted to the top
-                        const uint32_t h = __umulhi(G == 4 ? win : win << gsh, kBloomMul);
-                        const uint32_t word = h >> sh;
-                        if (MODE == MODE_CHECKED && word >= p.filt_words) {
-                            record_error(PM_ERR_BOUNDS);
-                            continue;
-                        }
-                        // both Bloom bits, each rotated down to bit 0 (the
-                        // funnel shift takes its amount mod 32)
-                        const uint32_t val = s_filt[word];
-                        const uint32_t r = __funnelshift_r(val, val, h) & __funnelshift_r(val, val, h >> 5);
-                        need |= (r & 1u) << q;
+        uint32_t s = 0, phase = 0;            // stage and its mbarrier phase
+        unsigned long long t0 = gw * p.tile;  // start of the current tile
+        const unsigned long long ahead = (unsigned long long)p.stages * tstride;
+        for (unsigned long long it = 0; it < my_tiles && !failed; ++it, t0 += tstride) {
+            const uint32_t nbytes = (uint32_t)tile_bytes(p, t0, end);
+            uint8_t *st = stages + (size_t)s * p.stage_bytes;
+
+            const bool ok = __all_sync(0xffffffffu, mbar_wait_bounded(&bars[s], phase));
+            if (!ok) {
+                if (lane == 0) {
+                    record_error(PM_ERR_TIMEOUT);
+                    // copies still in flight: tiles it .. it+stages-1
+                    for (unsigned long long j = 0; j < p.stages && it + j < my_tiles; ++j) {
+                        const uint32_t sj = (uint32_t)((s + j) % p.stages);
+                        mbar_wait_bounded(&bars[sj], phase ^ (uint32_t)((s + j) >= p.stages));
                     }
-                } else if (IDENT && KF >= 0) {
-                    const uint32_t w0 = wp[0];
-                    const uint32_t w1 = KF >= 1 ? wp[1] : 0u;
+                }
+                break;
+            }
+            const uint32_t nb16 = p.aligned ? (nbytes & ~15u) : 0u;
+            if (nb16 < nbytes) {
+                for (uint32_t i = nb16 + lane; i < nbytes; i += 32) st[i] = __ldg(p.text + t0 + i);
+                __syncwarp();
+            }
+
+            const uint32_t tile_n = (uint32_t)(total - t0 < p.tile ? total - t0 : p.tile);
+            uint32_t cur = 0;
+            unsigned long long text_end = end;
+            if (BATCH) {
+                cur = find_text(p.offsets, p.ntexts, t0 + 4 * lane < total ? t0 + 4 * lane : t0);
+                text_end = __ldg(p.offsets + cur + 1);
+            }
+            uint32_t rel_end = rel_end_of(text_end, t0);
+            // groups [lp0, lp0+4) with lp0 + 4 <= fast_n take the fast path
+            auto fast_bound = [&]() -> uint32_t {
+                const uint32_t r = rel_end >= gram - 1 ? rel_end - (gram - 1) : 0u;
+                return r < tile_n ? r : tile_n;
+            };
+            uint32_t fast_n = fast_bound();
+            int32_t *idt = p.ids + t0;  // this tile's ids
+
+            const uint32_t iters = (tile_n + 127) >> 7;
+            for (uint32_t i = 0; i < iters; ++i) {
+                const uint32_t lp0 = (i << 7) + 4 * lane;
+                const uint32_t *wp = reinterpret_cast<const uint32_t *>(st + lp0);
+                if (BATCH && lp0 < tile_n && t0 + lp0 >= text_end) {
+                    while (t0 + lp0 >= text_end) {
+                        ++cur;
+                        text_end = __ldg(p.offsets + cur + 1);
+                    }
+                    rel_end = rel_end_of(text_end, t0);
+                    fast_n = fast_bound();
+                }
+                const uint32_t cur0 = cur;  // text of position lp0
+                const uint32_t w0 = wp[0], w1 = wp[1];  // bytes lp0 .. lp0+7 (staged)
+                uint32_t need = 0;   // bit q: position lp0+q passed the filter
+                uint32_t rootm = 0;  // bit q: position lp0+q is walked from the root
+                if (MODE != MODE_LOOKUPS && lp0 + 4 <= fast_n) {
+                    // Fast path: four positions, all bytes up to lp0+3+gram-1
+                    // inside the text. The filter decides, in shared memory,
+                    // which positions can reach depth k+1.
+                    if (IDENT && KF >= (int)kBloomK) {
+                        // blocked Bloom test of the g-gram at each position
+                        const uint32_t sh = 32u - (8u * KFU + lw - 5u);
+                        const uint32_t gsh = G > 0 ? 32u - 8u * G : 32u - 8u * gram;
 #pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        const uint32_t x = q == 0 ? w0 : __funnelshift_r(w0, w1, 8 * q);
-                        const uint32_t idx = x & imask;
-                        const uint32_t word = idx >> 5;
-                        if (MODE == MODE_CHECKED && word >= p.filt_words) {
-                            record_error(PM_ERR_BOUNDS);
-                            continue;
+                        for (int q = 0; q < 4; ++q) {
+                            const uint32_t win = q == 0 ? w0 : __funnelshift_r(w0, w1, 8 * q);
+                            // bytes q .. q+g-1, shifted to the top
+                            const uint32_t h = __umulhi(G == 4 ? win : win << gsh, kBloomMul);
+                            const uint32_t word = h >> sh;
+                            if (MODE == MODE_CHECKED && word >= p.filt_words) {
+                                record_error(PM_ERR_BOUNDS);
+                                continue;
+                            }
+                            // both Bloom bits, each rotated down to bit 0 (the
+                            // funnel shift takes its amount mod 32)
+                            const uint32_t val = s_filt[word];
+                            const uint32_t r = __funnelshift_r(val, val, h) & __funnelshift_r(val, val, h >> 5);
+                            need |= (r & 1u) << q;
                         }
-                        need |= ((s_filt[word] >> (idx & 31u)) & 1u) << q;
+                    } else if (IDENT && KF >= 0) {
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            const uint32_t x = q == 0 ? w0 : __funnelshift_r(w0, w1, 8 * q);
+                            const uint32_t idx = x & imask;
+                            const uint32_t word = idx >> 5;
+                            if (MODE == MODE_CHECKED && word >= p.filt_words) {
+                                record_error(PM_ERR_BOUNDS);
+                                continue;
+                            }
+                            need |= ((s_filt[word] >> (idx & 31u)) & 1u) << q;
+                        }
+                    } else {
+                        uint32_t c[16];
+#pragma unroll
+                        for (int w = 0; w < 4; ++w) {
+                            const uint32_t word = w == 0 ? w0 : w == 1 ? w1 : (uint32_t)(4 * w) < k + 4 ? wp[w] : 0u;
+#pragma unroll
+                            for (int b = 0; b < 4; ++b)
+                                c[4 * w + b] = class_of<IDENT>(s_lut, lane, (word >> (8 * b)) & 0xFFu);
+                        }
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            uint32_t cd = 0, nc = 0;
+#pragma unroll
+                            for (int j = 0; j < 12; ++j) {
+                                if (j < (int)k) cd = cd * C + c[q + j];
+                                if (j == (int)k) nc = c[q + j];
+                            }
+                            if (k == 12) nc = c[q + 12];
+                            const uint32_t idx = (cd << lw) | (nc & wmask);
+                            const uint32_t word = idx >> 5;
+                            if (MODE == MODE_CHECKED && word >= p.filt_words) {
+                                record_error(PM_ERR_BOUNDS);
+                                continue;
+                            }
+                            need |= ((s_filt[word] >> (idx & 31u)) & 1u) << q;
+                        }
                     }
                 } else {
-                    uint32_t c[16];
-#pragma unroll
-                    for (int w = 0; w < 4; ++w) {
-                        const uint32_t word = (uint32_t)(4 * w) < k + 4 ? wp[w] : 0u;
-#pragma unroll
-                        for (int b = 0; b < 4; ++b)
-                            c[4 * w + b] = class_of<IDENT>(s_lut, lane, (word >> (8 * b)) & 0xFFu);
-                    }
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        uint32_t cd = 0, nc = 0;
-#pragma unroll
-                        for (int j = 0; j < 12; ++j) {
-                            if (j < (int)k) cd = cd * C + c[q + j];
-                            if (j == (int)k) nc = c[q + j];
+                    // ragged group (tile end, text boundary, last bytes of a
+                    // text): every position that passes the filter, or that
+                    // is too close to its text end to test, is walked from the
+                    // root
+                    for (uint32_t q = 0; q < 4; ++q) {
+                        const uint32_t lp = lp0 + q;
+                        if (lp >= tile_n) break;
+                        const unsigned long long pos = t0 + lp;
+                        if (BATCH) {
+                            while (pos >= text_end) {
+                                ++cur;
+                                text_end = __ldg(p.offsets + cur + 1);
+                            }
+                            rel_end = rel_end_of(text_end, t0);
+                            fast_n = fast_bound();
                         }
-                        if (k == 12) nc = c[q + 12];
-                        const uint32_t idx = (cd << lw) | (nc & wmask);
-                        const uint32_t word = idx >> 5;
+                        if (MODE == MODE_LOOKUPS || lp + gram > rel_end) {
+                            rootm |= 1u << q;
+                            continue;
+                        }
+                        uint32_t word, bits;
+                        if (IDENT && KF >= (int)kBloomK) {
+                            uint32_t x = 0;
+                            for (uint32_t j = 0; j < gram; ++j) x |= (uint32_t)st[lp + j] << (8 * j);
+                            const BloomProbe b = bloom_probe(x, gram, 8u * KFU + lw - 5u);
+                            word = b.word;
+                            bits = b.mask;
+                        } else if (IDENT && KF >= 0) {
+                            uint32_t x = 0;
+                            for (uint32_t j = 0; j <= k; ++j) x |= (uint32_t)st[lp + j] << (8 * j);
+                            const uint32_t idx = x & imask;
+                            word = idx >> 5;
+                            bits = 1u << (idx & 31u);
+                        } else {
+                            uint32_t cd = 0;
+                            for (uint32_t j = 0; j + 1 <= k; ++j) cd = cd * C + class_of<IDENT>(s_lut, lane, st[lp + j]);
+                            const uint32_t idx = (cd << lw) | (class_of<IDENT>(s_lut, lane, st[lp + k]) & wmask);
+                            word = idx >> 5;
+                            bits = 1u << (idx & 31u);
+                        }
                         if (MODE == MODE_CHECKED && word >= p.filt_words) {
                             record_error(PM_ERR_BOUNDS);
                             continue;
                         }
-                        need |= ((s_filt[word] >> (idx & 31u)) & 1u) << q;
+                        if ((s_filt[word] & bits) == bits) rootm |= 1u << q;
                     }
                 }
-            } else {
-                // ragged group (tile end, text boundary, last k bytes of a
-                // text): every position that passes the filter, or that is
-                // too close to its text end to test, is walked from the root
-                for (uint32_t q = 0; q < 4; ++q) {
-                    const uint32_t lp = lp0 + q;
-                    if (lp >= tile_n) break;
-                    const unsigned long long pos = t0 + lp;
-                    if (BATCH) {
-                        while (pos >= text_end) {
-                            ++cur;
-                            text_end = __ldg(p.offsets + cur + 1);
+                // every position gets -1 now; the walkers patch the matches
+                if (BATCH && p.out_ids) {
+                    // per-text output buffers: each position to its own text's
+                    uint32_t c2 = cur0;
+                    unsigned long long e2 = __ldg(p.offsets + c2 + 1);
+                    for (uint32_t q = 0; q < 4 && lp0 + q < tile_n; ++q) {
+                        const unsigned long long pos = t0 + lp0 + q;
+                        while (pos >= e2) {
+                            ++c2;
+                            e2 = __ldg(p.offsets + c2 + 1);
                         }
-                        rel_end = rel_end_of(text_end, t0);
-                        fast_n = fast_bound();
+                        __stcs(p.out_ids[c2] + (pos - __ldg(p.offsets + c2)), -1);
                     }
-                    if (MODE == MODE_LOOKUPS || lp + gram > rel_end) {
-                        rootm |= 1u << q;
-                        continue;
-                    }
-                    uint32_t word, bits;
-                    if (IDENT && KF >= (int)kBloomK) {
-                        uint32_t x = 0;
-                        for (uint32_t j = 0; j < gram; ++j) x |= (uint32_t)st[lp + j] << (8 * j);
-                        const BloomProbe b = bloom_probe(x, gram, 8u * KFU + lw - 5u);
-                        word = b.word;
-                        bits = b.mask;
-                    } else if (IDENT && KF >= 0) {
-                        uint32_t x = 0;
-                        for (uint32_t j = 0; j <= k; ++j) x |= (uint32_t)st[lp + j] << (8 * j);
-                        const uint32_t idx = x & imask;
-                        word = idx >> 5;
-                        bits = 1u << (idx & 31u);
-                    } else {
-                        uint32_t cd = 0;
-                        for (uint32_t j = 0; j + 1 <= k; ++j) cd = cd * C + class_of<IDENT>(s_lut, lane, st[lp + j]);
-                        const uint32_t idx = (cd << lw) | (class_of<IDENT>(s_lut, lane, st[lp + k]) & wmask);
-                        word = idx >> 5;
-                        bits = 1u << (idx & 31u);
-                    }
-                    if (MODE == MODE_CHECKED && word >= p.filt_words) {
-                        record_error(PM_ERR_BOUNDS);
-                        continue;
-                    }
-                    if ((s_filt[word] & bits) == bits) rootm |= 1u << q;
-                }
-            }
-            // every position gets -1 now; phase 2 patches the matches
-            if (BATCH && p.out_ids) {
-                // per-text output buffers: each position to its own text's
-                uint32_t c2 = cur0;
-                unsigned long long e2 = __ldg(p.offsets + c2 + 1);
-                for (uint32_t q = 0; q < 4 && lp0 + q < tile_n; ++q) {
-                    const unsigned long long pos = t0 + lp0 + q;
-                    while (pos >= e2) {
-                        ++c2;
-                        e2 = __ldg(p.offsets + c2 + 1);
-                    }
-                    __stcs(p.out_ids[c2] + (pos - __ldg(p.offsets + c2)), -1);
-                }
-            } else if (p.ids_aligned && lp0 + 4 <= tile_n) {
-                __stcs(reinterpret_cast<int4 *>(idt + lp0), make_int4(-1, -1, -1, -1));
-            } else {
+                } else if (p.ids_aligned && lp0 + 4 <= tile_n) {
+                    __stcs(reinterpret_cast<int4 *>(idt + lp0), make_int4(-1, -1, -1, -1));
+                } else {
 #pragma unroll
-                for (int q = 0; q < 4; ++q)
-                    if (lp0 + q < tile_n) __stcs(idt + lp0 + q, -1);
-            }
-            // warp ballot/popc compaction of the groups with work
-            const uint32_t work = need | rootm;
-            const uint32_t mg = __ballot_sync(0xffffffffu, work != 0);
-            if (mg) {
-                if (work)
-                    queue[qn + __popc(mg & ((1u << lane) - 1u))] =
-                        make_uint2(lp0 | (work << 16) | (rootm << 20), (uint32_t)it);
-                qn += __popc(mg);
-                if (qn >= kRound) {
-                    walk_queue<IDENT, BATCH, MODE>(p, queue, qn, gw, TW, end, k, s_lut, lane, acc,
-                                                   look);
-                    qn = 0;
+                    for (int q = 0; q < 4; ++q)
+                        if (lp0 + q < tile_n) __stcs(idt + lp0 + q, -1);
+                }
+                // warp ballot/popc compaction of the groups with work into
+                // the shared ring; the group's bytes travel with it
+                const uint32_t work = need | rootm;
+                const uint32_t mg = __ballot_sync(0xffffffffu, work != 0);
+                if (mg) {
+                    uint32_t base = 0;
+                    if (lane == 0) base = atomicAdd(&ring->wr, (unsigned)__popc(mg));
+                    base = __shfl_sync(0xffffffffu, base, 0);
+                    if (work) {
+                        const uint32_t slot = base + __popc(mg & ((1u << lane) - 1u));
+                        const uint32_t idx = slot & (kRing - 1);
+                        const long long w0c = clock64();
+                        bool free_slot = true;
+                        while (vf[idx] != slot) {  // until the cell is free for this slot
+                            if (clock64() - w0c > kWaitBudget) {
+                                record_error(PM_ERR_TIMEOUT);
+                                free_slot = false;
+                                break;
+                            }
+                        }
+                        if (free_slot) {
+                            const unsigned long long g0 = t0 + lp0;
+                            entries[idx] = make_uint4((uint32_t)g0,
+                                                      (uint32_t)(g0 >> 32) | (work << 24) | (rootm << 28),
+                                                      w0, w1);
+                            __threadfence_block();  // the -1 store and the entry before the flag
+                            vf[idx] = slot + 1u;
+                        } else {
+                            failed = true;
+                        }
+                    }
+                    failed = __any_sync(0xffffffffu, failed);
+                    if (failed) break;
                 }
             }
-        }
 
-        __syncwarp();  // stage s fully consumed by this warp
-        if (lane == 0 && it + p.stages < my_tiles) {
-            fence_proxy_async();
-            issue_tile(p, stages, bars, s, t0 + ahead, end);
+            __syncwarp();  // stage s fully consumed by this warp
+            if (failed) {
+                // drain this warp's copies still in flight (tiles it+1 ..
+                // it+stages-1) before leaving
+                if (lane == 0)
+                    for (unsigned long long j = 1; j < p.stages && it + j < my_tiles; ++j) {
+                        const uint32_t sj = (uint32_t)((s + j) % p.stages);
+                        mbar_wait_bounded(&bars[sj], phase ^ (uint32_t)((s + j) >= p.stages));
+                    }
+                break;
+            }
+            if (lane == 0) {
+                if (it + p.stages < my_tiles) {
+                    fence_proxy_async();
+                    issue_tile(p, stages, bars, s, t0 + ahead, end);
+                }
+                atomicAdd(&ring->progress, 1u);
+            }
+            if (++s == p.stages) {
+                s = 0;
+                phase ^= 1u;
+            }
         }
-        if (++s == p.stages) {
-            s = 0;
-            phase ^= 1u;
+        __syncwarp();
+        if (lane == 0) {
+            __threadfence_block();  // the last reservations before the done count
+            atomicAdd(&ring->pdone, 1u);
         }
     }
-    if (qn) walk_queue<IDENT, BATCH, MODE>(p, queue, qn, gw, TW, end, k, s_lut, lane, acc, look);
 
     // warp reductions: single-text count and lookups
 #pragma unroll
@@ -702,14 +851,14 @@ __global__ void pm_counts_scatter_kernel(const int64_t *counts, int64_t *const *
 uint32_t round16(uint64_t x) { return (uint32_t)((x + 15) & ~15ull); }
 
 struct Layout {
-    uint32_t off_dense, off_lut, off_warp, warp_bytes, off_queue, off_stages, stage_bytes, total;
+    uint32_t off_dense, off_lut, off_ring, off_warp, warp_bytes, off_stages, stage_bytes, total;
     uint32_t filt_u4, dense_u4, filt_words, halo;
 };
 
 int width_index(int32_t bits) { return bits == 8 ? 0 : bits == 16 ? 1 : 2; }
 
-// Shared memory: [filter][dense table][class LUT] shared by the CTA, then
-// one block per warp: [mbarriers][walk queue][stages x (tile + halo)].
+// Shared memory: [filter][dense table][class LUT][walk ring] shared by the CTA, then one
+// block per producer warp: [mbarriers][stages x (tile + halo)].
 Layout layout(const TrieDev &t, const pm_config &cfg)
 {
     Layout L{};
@@ -718,16 +867,20 @@ Layout layout(const TrieDev &t, const pm_config &cfg)
     L.filt_u4 = L.filt_words / 4;
     uint32_t off = round16((uint64_t)L.filt_words * 4);
     L.off_dense = off;
-    L.dense_u4 = 0;
+    L.dense_u4 = k > 0 ? t.dense_words[k] / 2 : 0;  // the walkers' depth-k lookups
+    off += L.dense_u4 * 16;
     L.off_lut = off;
     if (t.C != 256) off += 64 * 32 * 4;
+    L.off_ring = off;
+    off += kRing * 16 + kRing * 4 + (uint32_t)sizeof(Ring);
+    off = round16(off);
     L.off_warp = off;
     L.halo = round16(t.max_len > 16 ? t.max_len : 16);
     L.stage_bytes = (uint32_t)cfg.tile + L.halo;
-    L.off_queue = round16((uint64_t)kMaxStages * 8);
-    L.off_stages = L.off_queue + kQueue * 8;
+    L.off_stages = round16((uint64_t)kMaxStages * 8);
     L.warp_bytes = L.off_stages + (uint32_t)cfg.stages * L.stage_bytes;
-    L.total = off + (uint32_t)(cfg.threads / 32) * L.warp_bytes;
+    const uint32_t producers = (uint32_t)(cfg.threads / 32 - cfg.walkers);
+    L.total = off + producers * L.warp_bytes;
     return L;
 }
 
@@ -787,13 +940,14 @@ int launch_scan(const TrieDev &t, const pm_config &cfg, const ScanArgs &a, void 
     p.gram = t.gram[cfg.dense_k];
     p.binary = cfg.row_search ? 1u : 0u;
     p.stages = (uint32_t)cfg.stages;
+    p.walkers = (uint32_t)cfg.walkers;
     p.aligned = ((uintptr_t)a.text & 15u) == 0;
     p.ids_aligned = ((uintptr_t)a.ids & 15u) == 0;
     p.off_dense = L.off_dense;
     p.off_lut = L.off_lut;
+    p.off_ring = L.off_ring;
     p.off_warp = L.off_warp;
     p.warp_bytes = L.warp_bytes;
-    p.off_queue = L.off_queue;
     p.off_stages = L.off_stages;
     p.stage_bytes = L.stage_bytes;
     p.filt_u4 = L.filt_u4;
@@ -823,7 +977,7 @@ int launch_scan(const TrieDev &t, const pm_config &cfg, const ScanArgs &a, void 
     unsigned long long grid = (unsigned long long)device_sms * occ;
     const unsigned long long known = batch ? a.total_hint : a.len;
     if (known) {
-        const unsigned long long warps = cfg.threads / 32;
+        const unsigned long long warps = cfg.threads / 32 - cfg.walkers;
         unsigned long long ntiles = (known + cfg.tile - 1) / cfg.tile;
         unsigned long long need = (ntiles + warps - 1) / warps;
         if (need < grid) grid = need;

@@ -1,7 +1,7 @@
 """Autotuner for the scan's launch configuration.
 
-Times candidate `pm_config`s (threads per CTA, text bytes per warp tile,
-stages in flight, shared-memory filter level and width, row search) on a
+Times candidate `pm_config`s (threads per CTA, walker warps, text bytes per
+warp tile, stages in flight, shared-memory filter level and width) on a
 representative device input with CUDA events, keeps the fastest and installs
 it on the handle with pm_set_config. Results can be cached in a JSON file
 keyed by GPU name and trie shape (nodes, longest pattern, alphabet size, and
@@ -24,10 +24,13 @@ def candidates(trie: pm.Trie, total_bytes: int) -> List[dict]:
     kmax = st["dense_k_max"]
     ks = sorted({kmax, max(kmax - 1, 0)})
     out = []
-    for threads, tile, stages, k, bits, rs in itertools.product(
-            (1024, 512), (1024, 2048, 4096), (2, 3), ks, (8, 16, 32), (0, 1)):
+    for threads, tile, stages, k, bits, walkers in itertools.product(
+            (1024, 512), (1024, 2048, 4096), (2, 3), ks, (8, 16, 32), (2, 4, 8)):
+        if walkers >= threads // 32:
+            continue
         c = dict(base, threads=threads, tile=tile, stages=stages, dense_k=k,
-                 filter_bits=bits, row_search=rs, checked=0, ctas_per_sm=0)
+                 filter_bits=bits, row_search=0, checked=0, ctas_per_sm=0,
+                 walkers=walkers)
         try:
             pm.pm_set_config(trie, c)  # validates (shared memory, filter exists)
         except pm.PMError:

@@ -69,7 +69,7 @@ def assert_same(ids, cnt, o_ids, o_cnt):
 
 def small_cfg(trie, **kw):
     c = pm.pm_get_config(trie)
-    c.update(threads=128, tile=256, stages=2)
+    c.update(threads=128, tile=256, stages=2, walkers=1)
     c.update(kw)
     return c
 
@@ -125,7 +125,8 @@ def test_config_sweep():
                             c = dict(base, threads=threads, tile=tile, dense_k=k,
                                      filter_bits=bits, row_search=rs,
                                      stages=2 + (tile == 128) * 2,
-                                     checked=int(threads == 256))
+                                     checked=int(threads == 256),
+                                     walkers=1 + (rs + bits // 8) % (threads // 32 - 1))
                             try:
                                 pm.pm_set_config(t, c)
                             except pm.PMError:
