@@ -379,8 +379,8 @@ def main():
     stream = torch.cuda.current_stream()
 
     # trie-lookup count (instrumented kernel, outside the timed region) on
-    # the first 16 MiB of the text, scaled to the whole text
-    look_n = min(n, 16 << 20)
+    # the first 4 MiB of the text, scaled to the whole text
+    look_n = min(n, 4 << 20)
     look = torch.zeros(1, dtype=torch.int64, device="cuda")
     pm.pm_scan_ex(trie, text, None, ids, cnt, lookups=look, length=look_n)
     torch.cuda.synchronize()
