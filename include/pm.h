@@ -84,6 +84,10 @@ typedef struct {
     uint64_t dense256_bytes; /* uncompressed 256-wide state table: 256*4*n      */
     uint64_t bitmap36_bytes; /* 256-bit bitmap + 4-byte offset per node: 36*n   */
     uint64_t device_bytes;   /* everything the handle holds on the device      */
+    uint64_t deep_bytes;     /* deep level table (0 if none)                    */
+    uint32_t deep_k;         /* depth of the deep level read from L2: the root  */
+                             /* paths of that depth as a bitmap with ranks;     */
+                             /* byte-class tries only, 0 if none               */
 } pm_trie_stats;
 
 /* Launch configuration of the scan kernel (picked by an autotuner). The
@@ -103,6 +107,8 @@ typedef struct {
     int32_t checked;      /* 1: bounds-checked scan (PM_ERR_BOUNDS on error)  */
     int32_t walkers;      /* warps per CTA that run the CRS walks the others  */
                           /* queue, 1 .. threads/32 - 1                       */
+    int32_t deep;         /* 1: positions passing the filter look up the deep */
+                          /* level before walking (needs deep_k > 0), 0: not */
 } pm_config;
 
 /* ---- trie construction (Section III, steps I, II, VI and the CRS step) --
@@ -148,8 +154,9 @@ int pm_set_config(pm_trie *h, const pm_config *cfg);
  * pm_scan: one text d_text[0..len) (device memory, any alignment). Writes
  * out.ids[0..len) and *out.count, asynchronously on `stream`. len == 0 is
  * legal (count 0). The handle is read-only during scans, so concurrent scans
- * on different streams are safe; out.ids must not alias the text.
- * Errors: PM_ERR_INVAL (null pointers with len > 0), PM_ERR_HOST_ONLY,
+ * on different streams are safe; out.ids must not alias the text. A text
+ * (and a batch's total) is below 2^40 bytes.
+ * Errors: PM_ERR_INVAL (null pointers with len > 0, len >= 2^40), PM_ERR_HOST_ONLY,
  *         PM_ERR_CUDA (launch failed). */
 int pm_scan(const pm_trie *h, const uint8_t *d_text, uint64_t len,
             pm_result out, pm_stream stream);

@@ -70,11 +70,13 @@ int32_t pick_bits(const pm_trie *h, int32_t k)
     return 0;
 }
 
-// Default launch configuration: one 1024-thread CTA per SM (26 producer and
-// 6 walker warps), 1-2 KiB producer tiles double-buffered, the deepest
-// filter level that fits; for the byte alphabet's Bloom filter the wider
-// filter with smaller tiles comes first (fewer walks). An autotuner may
-// refine it.
+// Default launch configuration: one 1024-thread CTA per SM, 1-2 KiB
+// producer tiles double-buffered, the deepest filter level that fits; for
+// the byte alphabet's Bloom filter the wider filter with smaller tiles comes
+// first (fewer walks). The walker warps' share follows the expected share
+// of positions that need a walk: 3/16 of the warps behind the deep level
+// (with 1 KiB tiles), most of them when an exact filter passes most
+// positions, an eighth otherwise. An autotuner may refine it.
 pm_config default_config(const pm_trie *h, int smem_limit)
 {
     pm_config c{};
@@ -82,6 +84,7 @@ pm_config default_config(const pm_trie *h, int smem_limit)
     c.ctas_per_sm = 0;
     c.stages = 2;
     c.checked = 0;
+    c.deep = h->host.deep_k > 0 ? 1 : 0;
     const uint64_t limit = (uint64_t)smem_limit - 1024;
     struct Pref {
         int32_t bits, tile;
@@ -89,17 +92,38 @@ pm_config default_config(const pm_trie *h, int smem_limit)
     for (int32_t k = (int32_t)h->host.dense_k_max; k >= 0; --k) {
         c.dense_k = k;
         const bool bloom = h->host.C == 256 && k >= 2;
+        // Share of positions that pass an exact filter: the (k+1)-grams over
+        // the used classes that are root paths. Walkers get a share of the
+        // warps to match (the Bloom filter passes well under 1 %).
+        double pass = 0.0;
+        if (!bloom) {
+            double space = 1.0;
+            const double used = h->host.C == 256 ? 256.0 : (double)h->host.C - 1.0;
+            for (int32_t j = 0; j <= k; ++j) space *= std::max(used, 1.0);
+            const std::vector<uint32_t> &lv = h->host.level_nodes;
+            const double paths = (size_t)k + 1 < lv.size() ? lv[k + 1] : 0.0;
+            pass = std::min(1.0, paths / space);
+        }
         std::vector<Pref> prefs;
         if (bloom) prefs = {{16, 1024}, {8, 2048}, {8, 1536}, {8, 1024}};
         const int32_t exact = pick_bits(h, k);
-        for (int32_t tile : {2048, 1536, 1024, 512, 256, 128}) prefs.push_back({exact, tile});
+        if (c.deep) {
+            for (int32_t tile : {1024, 2048, 512, 256, 128}) prefs.push_back({exact, tile});
+        } else {
+            for (int32_t tile : {2048, 1536, 1024, 512, 256, 128}) prefs.push_back({exact, tile});
+        }
         for (int32_t threads : {1024, 512, 256, 128}) {
             for (const Pref &pf : prefs) {
                 if (!have_filter(h, k, pf.bits)) continue;
                 c.threads = threads;
                 c.tile = pf.tile;
                 c.filter_bits = pf.bits;
-                c.walkers = std::max<int32_t>(1, threads / 32 * 3 / 16);
+                const int32_t warps = threads / 32;
+                c.walkers = c.deep          ? warps * 3 / 16
+                            : pass > 0.3    ? warps * 7 / 8
+                            : pass > 0.05   ? warps / 2
+                                            : warps / 8;
+                c.walkers = std::min(std::max<int32_t>(1, c.walkers), warps - 1);
                 if (pm::scan_smem_bytes(h->dev, c) <= limit) return c;
             }
         }
@@ -146,6 +170,10 @@ int validate_config(const pm_trie *h, const pm_config &c, std::string &why)
         why = "row_search and checked are 0 or 1";
         return PM_ERR_INVAL;
     }
+    if (c.deep < 0 || c.deep > 1 || (c.deep == 1 && h->host.deep_k == 0)) {
+        why = "deep is 0, or 1 when the trie has a deep level";
+        return PM_ERR_INVAL;
+    }
     uint64_t need = pm::scan_smem_bytes(h->dev, c);
     if (need + 1024 > (uint64_t)max_smem_optin(h->device)) {
         why = "configuration needs " + std::to_string(need) + " bytes of shared memory";
@@ -165,6 +193,10 @@ void fill_dev_sizes(pm_trie *h)
     d.min_len = t.n_patterns ? t.min_len : 0xFFFFFFFFu;
     d.max_len = t.max_len;
     d.dense_k_max = t.dense_k_max;
+    d.deep_k = t.deep_k;
+    d.deep_U = t.deep_U;
+    d.deep_first = t.deep_first;
+    d.deep_words = (uint32_t)(t.deep.size() / 2);
     for (int k = 0; k <= pm::kMaxDenseK; ++k) {
         d.dense_words[k] = (uint32_t)(t.dense[k].size() / 2);
         d.first[k] = t.first[k];
@@ -186,6 +218,17 @@ int upload(pm_trie *h)
     };
     std::vector<int2> emit(n);
     for (uint64_t v = 0; v < n; ++v) emit[v] = make_int2(t.best[v], t.nfinal[v]);
+    // row records (first non-zero, length | has-match, first eight bytes);
+    // the device derives the next state e + 1 from the non-zero's index
+    std::vector<uint4> row(n);
+    for (uint64_t v = 0; v < n; ++v) {
+        const uint32_t r0 = t.row_ptr[v], deg = t.row_ptr[v + 1] - r0;
+        uint32_t lab[2] = {0, 0};
+        for (uint32_t i = 0; i < deg && i < 8; ++i) lab[i >> 2] |= (uint32_t)t.col[r0 + i] << (8 * (i & 3));
+        row[v] = make_uint4(r0, deg | (t.nfinal[v] > 0 ? 1u << 31 : 0u), lab[0], lab[1]);
+    }
+    for (uint64_t e = 0; e < nnz; ++e)
+        if (t.next[e] != (int32_t)(e + 1)) return fail(PM_ERR_INVAL, "internal: next state is not BFS order");
     std::vector<Part> parts;
     uint64_t off = 0;
     auto add = [&](const void *src, uint64_t bytes) {
@@ -193,11 +236,11 @@ int upload(pm_trie *h)
         off = align256(off + std::max<uint64_t>(bytes, 16));
         return parts.size() - 1;
     };
-    size_t i_row = add(t.row_ptr.data(), 4 * (n + 1));
+    size_t i_row = add(row.data(), 16 * n);
     size_t i_col = add(t.col.data(), nnz);
-    size_t i_next = add(t.next.data(), 4 * nnz);
     size_t i_emit = add(emit.data(), 8 * n);
     size_t i_cls = add(t.cls, 256);
+    const size_t i_deep = t.deep.empty() ? (size_t)-1 : add(t.deep.data(), 4 * t.deep.size());
     const size_t none = (size_t)-1;
     size_t i_dense[pm::kMaxDenseK + 1];
     size_t i_f[pm::kMaxDenseK + 1][pm::kFilterWidths];
@@ -226,11 +269,11 @@ int upload(pm_trie *h)
         if (e != cudaSuccess) return cuda_fail("cudaMemcpy", e);
     }
     pm::TrieDev &d = h->dev;
-    d.row_ptr = reinterpret_cast<const uint32_t *>(base + parts[i_row].off);
+    d.row = reinterpret_cast<const uint4 *>(base + parts[i_row].off);
     d.col = base + parts[i_col].off;
-    d.next = reinterpret_cast<const int32_t *>(base + parts[i_next].off);
     d.emit = reinterpret_cast<const int2 *>(base + parts[i_emit].off);
     d.cls = base + parts[i_cls].off;
+    d.deep = i_deep == (size_t)-1 ? nullptr : reinterpret_cast<const uint2 *>(base + parts[i_deep].off);
     for (int k = 0; k <= pm::kMaxDenseK; ++k) {
         d.dense[k] = i_dense[k] == none ? nullptr
                                         : reinterpret_cast<const uint2 *>(base + parts[i_dense[k]].off);
@@ -286,6 +329,7 @@ int scan_common(const pm_trie *h, const uint8_t *d_texts, const uint64_t *d_offs
     if (!d_counts) return fail(PM_ERR_INVAL, "counts is NULL");
     if (batch ? ntexts > 0 && (!d_texts || !d_ids) : len > 0 && (!d_texts || !d_ids))
         return fail(PM_ERR_INVAL, "text or ids is NULL");
+    if (!batch && len >= (1ull << 40)) return fail(PM_ERR_INVAL, "text of 2^40 bytes or more");
     pm_config c = cfg ? *cfg : h->cfg;
     if (cfg) {
         std::string why;
@@ -371,6 +415,8 @@ int pm_stats(const pm_trie *h, pm_trie_stats *s)
     s->dense256_bytes = 256ull * 4 * n;
     s->bitmap36_bytes = 36ull * n;
     s->device_bytes = h->device_bytes;
+    s->deep_bytes = 4ull * t.deep.size();
+    s->deep_k = t.deep_k;
     return ok();
 }
 

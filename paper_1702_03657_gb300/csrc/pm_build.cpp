@@ -174,6 +174,8 @@ int build_host_trie(const uint8_t *const *patterns, const uint32_t *lengths,
         t.row_ptr.push_back((uint32_t)t.col.size());
     }
     const uint32_t nn = (uint32_t)rng.size();
+    t.level_nodes.assign(t.max_len + 1, 0);
+    for (uint32_t v = 0; v < nn; ++v) ++t.level_nodes[t.depth[v]];
 
     // Top-level tables for k = 0 .. K, K < shortest pattern, so that no
     // pattern ends within the levels a table resolves.
@@ -270,6 +272,52 @@ int build_host_trie(const uint8_t *const *patterns, const uint32_t *lengths,
                     f[bit >> 5] |= 1u << (bit & 31);
                 }
             }
+        }
+    }
+
+    // Deep level (byte classes): the root paths of depth D2, K + 2 <= D2 <
+    // shortest pattern, as a bitmap with ranks over base-U codes, U = the
+    // used classes (a byte of the "other" class is on no path). A position
+    // whose D2-gram is not a root path cannot match (D2 < shortest
+    // pattern); one that is starts its walk at depth D2.
+    t.deep_k = t.deep_U = t.deep_first = 0;
+    t.deep.clear();
+    if (!le && m > 0) {
+        const uint32_t U = t.C - 1;
+        uint32_t D2 = 0;
+        for (uint32_t d = K + 2; d <= std::min<uint32_t>(t.min_len - 1, kDeepMaxK); ++d) {
+            if (ipow_capped(U, (int)d, kDeepCodes) == 0) break;
+            D2 = d;
+        }
+        if (D2) {
+            std::vector<uint64_t> code2(nn, 0);
+            uint32_t first2 = 0;
+            for (uint32_t d = 0; d < D2; ++d) first2 += t.level_nodes[d];
+            for (uint32_t v = 0; v < first2; ++v)  // BFS: nodes above depth D2
+                for (uint32_t e = t.row_ptr[v]; e < t.row_ptr[v + 1]; ++e)
+                    code2[t.next[e]] = code2[v] * U + t.cls[t.col[e]];
+            const uint64_t codes = ipow_capped(U, (int)D2, ~0ull);
+            uint64_t words = (codes + 31) / 32;
+            words += words & 1;
+            t.deep.assign(2 * words, 0);
+            uint64_t prev = 0;
+            for (uint32_t i = 0; i < t.level_nodes[D2]; ++i) {
+                const uint64_t c = code2[first2 + i];
+                if (t.depth[first2 + i] != D2 || (i > 0 && c <= prev)) {
+                    msg = "internal: deep level not in code order";
+                    return PM_ERR_INVAL;
+                }
+                prev = c;
+                t.deep[2 * (c >> 5)] |= 1u << (c & 31);
+            }
+            uint32_t run = 0;
+            for (uint64_t w = 0; w < words; ++w) {
+                t.deep[2 * w + 1] = run;
+                run += (uint32_t)__builtin_popcount(t.deep[2 * w]);
+            }
+            t.deep_k = D2;
+            t.deep_U = U;
+            t.deep_first = first2;
         }
     }
     return PM_OK;

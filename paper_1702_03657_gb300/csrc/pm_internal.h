@@ -19,6 +19,11 @@ constexpr int kMaxDenseK = 12;
 constexpr uint64_t kDenseBudget = 1u << 20;
 // Shared-memory budget of one filter table.
 constexpr uint64_t kFilterBudget = 128u * 1024u;
+// Deep level (byte classes only): the root paths of one depth between the
+// shared-memory levels and the shortest pattern, as a bitmap with ranks read
+// from L2; at most 2^26 codes (16 MiB) and depth 13 (the producer's window).
+constexpr uint64_t kDeepCodes = 1ull << 26;
+constexpr uint32_t kDeepMaxK = 13;
 // Filter widths: W = 8, 16, 32 bits per k-gram (index 0, 1, 2).
 constexpr int kFilterWidths = 3;
 
@@ -77,10 +82,16 @@ __host__ __device__ inline BloomProbe bloom_probe(uint32_t x, uint32_t gram, uin
 // mod W; bits of k-grams that are not root paths are clear. It is exact
 // when C <= W. With k < shortest pattern, a clear bit proves that the walk
 // from this start position stops at depth <= k without a match.
+// Device form of the CRS matrix. BFS numbering makes the next state of
+// non-zero e equal to e + 1, so the value array is implicit, and each row is
+// described by one 16-byte record read in a single load per walk step:
+//   x: index of the row's first non-zero (row_ptr[v])
+//   y: row length (bits 0..8) | 1 << 31 when a pattern ends on v's path
+//   z, w: the row's first eight column bytes, ascending (zero padded)
+// col holds every row's bytes for rows longer than eight.
 struct TrieDev {
-    const uint32_t *row_ptr;
+    const uint4 *row;
     const uint8_t *col;
-    const int32_t *next;
     const int2 *emit;
     const uint8_t *cls;                                   // byte -> class
     const uint2 *dense[kMaxDenseK + 1];                   // index k (0 unused)
@@ -96,6 +107,11 @@ struct TrieDev {
     uint32_t min_len;                                     // shortest pattern (>= 1)
     uint32_t max_len;
     uint32_t dense_k_max;                                 // deepest filter level
+    const uint2 *deep;                                    // deep level {bits, base} (or null)
+    uint32_t deep_k;                                      // its depth (0: none)
+    uint32_t deep_U;                                      // its code base: used classes
+    uint32_t deep_first;                                  // BFS id of the first depth-deep_k node
+    uint32_t deep_words;                                  // uint2 entries
 };
 
 // Host-side trie: the CRS arrays plus the derived tables.
@@ -112,10 +128,13 @@ struct HostTrie {
     uint32_t min_len = 0, max_len = 0;
     uint64_t n_patterns = 0, n_duplicates = 0;
     uint32_t dense_k_max = 0;
+    uint32_t deep_k = 0, deep_U = 0, deep_first = 0;
+    std::vector<uint32_t> deep;  // interleaved {bits, base} over deep_U^deep_k codes
     std::vector<uint32_t> dense[kMaxDenseK + 1];     // interleaved {bits, base}
     std::vector<uint32_t> filter[kMaxDenseK + 1][kFilterWidths];
     uint32_t first[kMaxDenseK + 1] = {};
     uint32_t nlevel[kMaxDenseK + 1] = {};
+    std::vector<uint32_t> level_nodes;  // nodes per depth, every depth
     uint32_t gram[kMaxDenseK + 1] = {};  // bytes a level-k filter tests: k+1 or k+2
 };
 

@@ -60,6 +60,9 @@ struct KParams {
     const uint32_t *filter;     // filter table of level k, width W (global)
     const uint2 *dense;         // dense table of level k (k >= 1, global)
     uint32_t first_k;           // BFS id of the first depth-k node
+    uint32_t ck1;               // C^(k-1) (k >= 1): weight of a k-gram's first class
+    uint32_t kload;             // byte classes: classes a group reads (k or deep_k, + 4)
+    uint32_t deep_on;           // look up the deep level before walking
     uint32_t gram;              // bytes the filter tests per position (k+1 or k+2)
     uint32_t tile;
     uint32_t halo;
@@ -169,6 +172,24 @@ __device__ __forceinline__ uint32_t ld_trie_u32(const void *ptr, uint64_t pol)
     return v;
 }
 
+__device__ __forceinline__ uint4 ld_trie_u4(const uint4 *ptr, uint64_t pol)
+{
+    uint4 v;
+    asm("ld.global.nc.L2::cache_hint.v4.u32 {%0, %1, %2, %3}, [%4], %5;"
+        : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+        : "l"(ptr), "l"(pol));
+    return v;
+}
+
+__device__ __forceinline__ uint2 ld_trie_u2(const uint2 *ptr, uint64_t pol)
+{
+    uint2 v;
+    asm("ld.global.nc.L2::cache_hint.v2.u32 {%0, %1}, [%2], %3;"
+        : "=r"(v.x), "=r"(v.y)
+        : "l"(ptr), "l"(pol));
+    return v;
+}
+
 __device__ __forceinline__ uint32_t ld_trie_u8(const void *ptr, uint64_t pol)
 {
     uint32_t v;
@@ -240,65 +261,47 @@ __device__ __forceinline__ bool spin_ok(long long t0)
     return clock64() - t0 < kWaitBudget;
 }
 
-// Walk the CRS rows from node v with the text byte at j until the first
-// mismatch or the text end (Section II-C). Bytes [wpos, wpos+8) come from
-// the group's window; later ones from global memory. The byte and the row
-// bounds are fetched together, then the first column entry and its next
-// state. Returns the deepest node; j is advanced past the matched bytes.
-template <int MODE>
-__device__ __forceinline__ uint32_t crs_walk(const TrieDev &t, const uint8_t *text,
-                                             unsigned long long wpos, unsigned long long win,
-                                             unsigned long long &j, unsigned long long tend,
-                                             uint32_t v, uint32_t binary, unsigned long long &look)
+// Position of byte b in the CRS row [r0, r0 + deg) whose first eight bytes
+// (ascending, zero padded) are packed in lab0/lab1, or 0xFFFFFFFF. Bytes
+// past the eighth are searched in col by halving (rows longer than 16, or
+// `binary`) or in order.
+__device__ __forceinline__ uint32_t row_find(const uint8_t *col, uint32_t r0, uint32_t deg,
+                                             uint32_t lab0, uint32_t lab1, uint32_t b,
+                                             uint32_t binary, uint64_t pol)
 {
-    const uint64_t pol = policy_evict_last();
-    while (j < tend) {
-        if (MODE == MODE_CHECKED && v >= t.n_nodes) {
-            record_error(PM_ERR_BOUNDS);
-            break;
-        }
-        const unsigned long long d = j - wpos;
-        const uint32_t b = d < 8 ? (uint32_t)(win >> (8 * d)) & 0xFFu : (uint32_t)__ldg(text + j);
-        const uint32_t r0 = ld_trie_u32(t.row_ptr + v, pol), r1 = ld_trie_u32(t.row_ptr + v + 1, pol);
-        if (MODE == MODE_CHECKED && (r1 < r0 || r1 > t.nnz)) {
-            record_error(PM_ERR_BOUNDS);
-            break;
-        }
-        if (MODE == MODE_LOOKUPS) ++look;
-        if (r1 == r0) break;  // leaf
-        const uint32_t c0 = ld_trie_u8(t.col + r0, pol);
-        const uint32_t n0 = ld_trie_u32(t.next + r0, pol);
-        if (c0 == b) {
-            v = n0;
-            ++j;
-            continue;
-        }
-        if (c0 > b || r1 - r0 == 1) break;
-        uint32_t e;
-        bool found = false;
-        if (binary || r1 - r0 > 16) {  // long rows are always searched by halving
-            uint32_t lo = r0 + 1, hi = r1;
-            while (lo < hi) {
-                const uint32_t mid = (lo + hi) >> 1;
-                if (ld_trie_u8(t.col + mid, pol) < b) lo = mid + 1;
-                else hi = mid;
-            }
-            e = lo;
-            found = lo < r1 && ld_trie_u8(t.col + lo, pol) == b;
+    if (deg <= 8u || b <= (lab1 >> 24)) {
+        // labels are unique and ascending, padding sits above the row's end:
+        // the lowest zero byte of (labels xor b) is the match. The zero-byte
+        // test (x - 0x01..) & ~x & 0x80.. flags every zero byte and, through
+        // borrows, only bytes above one, so its lowest flag is exact.
+        const uint32_t bb = b * 0x01010101u;
+        const uint32_t x0 = lab0 ^ bb;
+        const uint32_t z0 = (x0 - 0x01010101u) & ~x0 & 0x80808080u;
+        uint32_t i;
+        if (z0 || deg <= 4u) {
+            i = z0 ? (uint32_t)(__ffs(z0) - 1) >> 3 : 8u;
         } else {
-            for (e = r0 + 1; e < r1; ++e) {
-                const uint32_t cb = ld_trie_u8(t.col + e, pol);
-                if (cb >= b) {
-                    found = cb == b;
-                    break;
-                }
-            }
+            const uint32_t x1 = lab1 ^ bb;
+            const uint32_t z1 = (x1 - 0x01010101u) & ~x1 & 0x80808080u;
+            i = z1 ? 4u + ((uint32_t)(__ffs(z1) - 1) >> 3) : 8u;
         }
-        if (!found) break;
-        v = ld_trie_u32(t.next + e, pol);
-        ++j;
+        return i < min(deg, 8u) ? r0 + i : 0xFFFFFFFFu;
     }
-    return v;
+    const uint32_t r1 = r0 + deg;
+    if (binary || deg > 16u) {
+        uint32_t lo = r0 + 8u, hi = r1;
+        while (lo < hi) {
+            const uint32_t mid = (lo + hi) >> 1;
+            if (ld_trie_u8(col + mid, pol) < b) lo = mid + 1;
+            else hi = mid;
+        }
+        return lo < r1 && ld_trie_u8(col + lo, pol) == b ? lo : 0xFFFFFFFFu;
+    }
+    for (uint32_t e = r0 + 8u; e < r1; ++e) {
+        const uint32_t cb = ld_trie_u8(col + e, pol);
+        if (cb >= b) return cb == b ? e : 0xFFFFFFFFu;
+    }
+    return 0xFFFFFFFFu;
 }
 
 // End of the current text relative to the tile start, clipped to 32 bits.
@@ -316,88 +319,94 @@ __device__ __forceinline__ uint32_t class_of(const uint32_t *s_lut, uint32_t lan
     return (s_lut[(b >> 2) * 32 + lane] >> ((b & 3) * 8)) & 0xFFu;
 }
 
-// One lane walks the flagged positions of a ring entry: each from its
-// depth-k node (k-gram code from the window, node from the dense table; a
-// k-gram that is not a root path stops the walk above depth k, without a
-// match) or from the root. A walk that finds a match patches its position's
-// id and adds its count.
-template <bool IDENT, bool BATCH, int MODE>
-__device__ __forceinline__ void walk_group(const KParams &p, uint4 e, unsigned long long end,
-                                           uint32_t k, const uint32_t *s_lut, const uint2 *s_dense,
-                                           uint32_t lane, unsigned long long &acc,
-                                           unsigned long long &look)
+// A walk from position pos ended at node v after matching `depth` bytes;
+// has: v's has-match bit (2: not read). Writes the position's id and adds
+// its count when a pattern ends on the path.
+template <bool BATCH>
+__device__ __forceinline__ void emit_walk(const KParams &p, unsigned long long pos, uint32_t txt,
+                                          uint32_t v, uint32_t depth, uint32_t has,
+                                          unsigned long long &acc)
 {
-    const TrieDev &t = p.t;
-    const unsigned long long g0 = ((unsigned long long)(e.y & 0xFFFFFFu) << 32) | e.x;
-    const unsigned long long win = ((unsigned long long)e.w << 32) | e.z;
-    uint32_t m = (e.y >> 24) & 0xFu;
-    const uint32_t rootm = e.y >> 28;
-    unsigned long long tend = end;
-    uint32_t txt = 0;
-    if (BATCH) {
-        txt = find_text(p.offsets, p.ntexts, g0 + (__ffs(m) - 1));
-        tend = __ldg(p.offsets + txt + 1);
-    }
-    while (m) {
-        const uint32_t q = __ffs(m) - 1;
-        m &= m - 1;
-        const unsigned long long pos = g0 + q;
-        if (BATCH) {
-            while (pos >= tend) {
-                ++txt;
-                tend = __ldg(p.offsets + txt + 1);
-            }
-        }
-        uint32_t v = 0;
-        unsigned long long j = pos;
-        if (!((rootm >> q) & 1u) && k > 0) {
-            uint32_t code = 0;
-            for (uint32_t j2 = 0; j2 < k; ++j2) {
-                const uint32_t d = q + j2;
-                const uint32_t b = d < 8 ? (uint32_t)(win >> (8 * d)) & 0xFFu : (uint32_t)__ldg(p.text + pos + j2);
-                code = code * t.C + class_of<IDENT>(s_lut, lane, b);
-            }
-            if (MODE == MODE_CHECKED && (code >> 5) >= p.dense_u4 * 2) {
-                record_error(PM_ERR_BOUNDS);
-                continue;
-            }
-            const uint2 d = s_dense[code >> 5];
-            const uint32_t bit = code & 31u;
-            if (!((d.x >> bit) & 1u)) continue;
-            v = p.first_k + d.y + __popc(d.x & ((1u << bit) - 1u));
-            j = pos + k;
-        }
-        v = crs_walk<MODE>(t, p.text, g0, win, j, tend, v, p.binary, look);
-        if (j - pos >= t.min_len) {
-            const int2 em = __ldg(t.emit + v);
-            if (em.y) {
-                if (BATCH && p.out_ids)
-                    p.out_ids[txt][pos - __ldg(p.offsets + txt)] = em.x;
-                else
-                    p.ids[pos] = em.x;
-                if (BATCH)
-                    atomicAdd(reinterpret_cast<unsigned long long *>(p.counts + txt),
-                              (unsigned long long)em.y);
-                else
-                    acc += (unsigned)em.y;
-            }
-        }
-    }
+    if (depth < p.t.min_len || has == 0u) return;
+    const int2 em = __ldg(p.t.emit + v);
+    if (!em.y) return;
+    if (BATCH && p.out_ids)
+        p.out_ids[txt][pos - __ldg(p.offsets + txt)] = em.x;
+    else
+        p.ids[pos] = em.x;
+    if (BATCH)
+        atomicAdd(reinterpret_cast<unsigned long long *>(p.counts + txt), (unsigned long long)em.y);
+    else
+        acc += (unsigned)em.y;
 }
 
-// Walker warp: takes up to 32 ring entries at a time, one per lane, until
-// every producer warp has finished and the ring is empty.
-template <bool IDENT, bool BATCH, int MODE>
+// A ring entry is one walk: the start position (40 bits), the bytes already
+// matched from it (its start depth: 0, k or the deep level's), the node at
+// that depth, and (batch) the index of its text, or 0xFFFFFFFF if unknown.
+__device__ __forceinline__ uint4 walk_entry_of(unsigned long long pos, uint32_t depth,
+                                               uint32_t node, uint32_t txt)
+{
+    return make_uint4((uint32_t)pos, ((uint32_t)(pos >> 32) & 0xFFu) | (depth << 8), node, txt);
+}
+
+// Run one walk (Section II-C): from its start node, read each node's row
+// record and the next text byte together, move to the child on that byte,
+// and stop at a mismatch, a leaf or the text end; then patch the
+// position's id when a pattern ends on the path.
+template <bool BATCH, int MODE>
+__device__ __forceinline__ void run_walk(const KParams &p, uint4 e, unsigned long long end,
+                                         uint64_t pol, unsigned long long &acc,
+                                         unsigned long long &look)
+{
+    const TrieDev &t = p.t;
+    const unsigned long long pos = ((unsigned long long)(e.y & 0xFFu) << 32) | e.x;
+    uint32_t jo = e.y >> 8;
+    uint32_t v = e.z;
+    uint32_t txt = 0;
+    unsigned long long tend = end;
+    if (BATCH) {
+        txt = e.w != 0xFFFFFFFFu ? e.w : find_text(p.offsets, p.ntexts, pos);
+        tend = __ldg(p.offsets + txt + 1);
+    }
+    const uint32_t te = rel_end_of(tend, pos);
+    const uint8_t *tp = p.text + pos;
+    uint32_t has = 2u;  // has-match bit of the final node (2: not read)
+    while (jo < te) {
+        if (MODE == MODE_CHECKED && v >= t.n_nodes) {
+            record_error(PM_ERR_BOUNDS);
+            return;
+        }
+        const uint32_t b = __ldg(tp + jo);
+        const uint4 r = ld_trie_u4(t.row + v, pol);
+        const uint32_t deg = r.y & 0x1FFu;
+        has = r.y >> 31;
+        if (MODE == MODE_CHECKED && (r.x > t.nnz || deg > t.nnz - r.x)) {
+            record_error(PM_ERR_BOUNDS);
+            return;
+        }
+        if (MODE == MODE_LOOKUPS) ++look;
+        if (deg == 0) break;  // leaf
+        const uint32_t ei = row_find(t.col, r.x, deg, r.z, r.w, b, p.binary, pol);
+        if (ei == 0xFFFFFFFFu) break;
+        v = ei + 1u;  // BFS order: the child of non-zero e is node e + 1
+        ++jo;
+        has = 2u;
+    }
+    emit_walk<BATCH>(p, pos, txt, v, jo, has, acc);
+}
+
+// Walker warp: takes up to 32 ring entries at a time, one walk per lane,
+// until every producer warp has finished and the ring is empty; the wait
+// for entries is bounded, counted from the producers' last progress.
+template <bool BATCH, int MODE>
 __device__ __forceinline__ void walker_loop(const KParams &p, Ring *ring, const uint4 *entries,
                                             unsigned int *flags, uint32_t NP,
-                                            unsigned long long end, uint32_t k,
-                                            const uint32_t *s_lut, const uint2 *s_dense,
-                                            uint32_t lane, unsigned long long &acc,
-                                            unsigned long long &look)
+                                            unsigned long long end, uint32_t lane,
+                                            unsigned long long &acc, unsigned long long &look)
 {
     volatile Ring *vr = ring;
     volatile unsigned int *vf = flags;
-    // the idle wait is bounded, counted from the producers' last progress
+    const uint64_t pol = policy_evict_last();
     long long t0 = clock64();
     uint32_t seen = vr->progress;
     while (true) {
@@ -453,7 +462,7 @@ __device__ __forceinline__ void walker_loop(const KParams &p, Ring *ring, const 
                 const uint4 e = entries[idx];
                 __threadfence_block();
                 vf[idx] = slot + kRing;  // free for the slot one lap later
-                walk_group<IDENT, BATCH, MODE>(p, e, end, k, s_lut, s_dense, lane, acc, look);
+                run_walk<BATCH, MODE>(p, e, end, pol, acc, look);
             }
         }
         __syncwarp();
@@ -514,8 +523,7 @@ __global__ void __launch_bounds__(1024, 1) pfac_scan_kernel(const KParams p)
     unsigned long long look = 0;  // lookups (MODE_LOOKUPS)
 
     if (warp >= NP) {
-        walker_loop<IDENT, BATCH, MODE>(p, ring, entries, flags, NP, end, k, s_lut, s_dense, lane,
-                                        acc, look);
+        walker_loop<BATCH, MODE>(p, ring, entries, flags, NP, end, lane, acc, look);
     } else {
         const unsigned long long gw = (unsigned long long)blockIdx.x * NP + warp;
         const unsigned long long TW = (unsigned long long)gridDim.x * NP;
@@ -537,6 +545,7 @@ __global__ void __launch_bounds__(1024, 1) pfac_scan_kernel(const KParams p)
         __syncwarp();
 
         const uint32_t C = t.C;
+        const uint64_t tpol = policy_evict_last();  // deep-level lookups
         const uint32_t lw = p.lw;
         const uint32_t wmask = (1u << lw) - 1u;
         // IDENT: filter bit index = low 8k+lw bits of the little-endian window
@@ -599,6 +608,8 @@ __global__ void __launch_bounds__(1024, 1) pfac_scan_kernel(const KParams p)
                 const uint32_t cur0 = cur;  // text of position lp0
                 const uint32_t w0 = wp[0], w1 = wp[1];  // bytes lp0 .. lp0+7 (staged)
                 uint32_t need = 0;   // bit q: position lp0+q passed the filter
+                uint32_t rk[4] = {0u, 0u, 0u, 0u};  // node ranks in the start level
+                uint32_t deepm = 0;  // bit q: position lp0+q starts at the deep level
                 uint32_t rootm = 0;  // bit q: position lp0+q is walked from the root
                 if (MODE != MODE_LOOKUPS && lp0 + 4 <= fast_n) {
                     // Fast path: four positions, all bytes up to lp0+3+gram-1
@@ -637,30 +648,124 @@ __global__ void __launch_bounds__(1024, 1) pfac_scan_kernel(const KParams p)
                             need |= ((s_filt[word] >> (idx & 31u)) & 1u) << q;
                         }
                     } else {
-                        uint32_t c[16];
+                        // byte classes: the k-gram code of position lp0 by
+                        // Horner's rule, then rolled one position at a time
+                        // (drop the first class, append the next); a position
+                        // that passes the filter gets the rank of its depth-k
+                        // node from the dense table
+                        uint32_t cw[4];  // classes of bytes lp0 .. lp0+15, four to a word
 #pragma unroll
                         for (int w = 0; w < 4; ++w) {
-                            const uint32_t word = w == 0 ? w0 : w == 1 ? w1 : (uint32_t)(4 * w) < k + 4 ? wp[w] : 0u;
+                            const uint32_t word = w == 0 ? w0 : w == 1 ? w1 : (uint32_t)(4 * w) < p.kload ? wp[w] : 0u;
+                            cw[w] = 0;
 #pragma unroll
                             for (int b = 0; b < 4; ++b)
-                                c[4 * w + b] = class_of<IDENT>(s_lut, lane, (word >> (8 * b)) & 0xFFu);
+                                cw[w] |= class_of<IDENT>(s_lut, lane, (word >> (8 * b)) & 0xFFu) << (8 * b);
                         }
+                        // class of byte lp0 + j (j known at compile time)
+#define PM_CLS(j) ((cw[(j) >> 2] >> (8 * ((j) & 3))) & 0xFFu)
+                        uint32_t cd = 0;
+#pragma unroll
+                        for (int j = 0; j < 12; ++j)
+                            if (j < (int)k) cd = cd * C + PM_CLS(j);
+                        // classes k .. k+3: the byte after each position's k-gram
+                        const uint32_t kw = k >> 2;
+                        const uint32_t wa = kw == 0 ? cw[0] : kw == 1 ? cw[1] : kw == 2 ? cw[2] : cw[3];
+                        const uint32_t wb = kw == 0 ? cw[1] : kw == 1 ? cw[2] : cw[3];
+                        const uint32_t nc4 = __funnelshift_r(wa, wb, 8u * (k & 3u));
 #pragma unroll
                         for (int q = 0; q < 4; ++q) {
-                            uint32_t cd = 0, nc = 0;
-#pragma unroll
-                            for (int j = 0; j < 12; ++j) {
-                                if (j < (int)k) cd = cd * C + c[q + j];
-                                if (j == (int)k) nc = c[q + j];
-                            }
-                            if (k == 12) nc = c[q + 12];
+                            const uint32_t nc = (nc4 >> (8 * q)) & 0xFFu;
                             const uint32_t idx = (cd << lw) | (nc & wmask);
                             const uint32_t word = idx >> 5;
                             if (MODE == MODE_CHECKED && word >= p.filt_words) {
                                 record_error(PM_ERR_BOUNDS);
+                            } else if ((s_filt[word] >> (idx & 31u)) & 1u) {
+                                if (k == 0) {
+                                    need |= 1u << q;
+                                } else if (MODE == MODE_CHECKED && (cd >> 5) >= p.dense_u4 * 2) {
+                                    record_error(PM_ERR_BOUNDS);
+                                } else {
+                                    const uint2 d = s_dense[cd >> 5];
+                                    const uint32_t bit = cd & 31u;
+                                    if ((d.x >> bit) & 1u) {
+                                        need |= 1u << q;
+                                        rk[q] = d.y + __popc(d.x & ((1u << bit) - 1u));
+                                    }
+                                }
+                            }
+                            if (q < 3 && k > 0) cd = (cd - PM_CLS(q) * p.ck1) * C + nc;
+                        }
+                        if (p.deep_on && need) {
+                            // deep level: a flagged position whose first
+                            // deep_k bytes lie in its text looks up its
+                            // deep_k-gram (base U, first class most
+                            // significant) in L2. A byte of the "other" class
+                            // or a gram that is not a root path means no match
+                            // (deep_k < shortest pattern); else the walk
+                            // starts at depth deep_k.
+                            const uint32_t K2 = t.deep_k, U = t.deep_U;
+                            uint32_t om = 0;  // bit j: the byte at lp0 + j is of the "other" class
+#pragma unroll
+                            for (int j = 0; j < 16; ++j) om |= (uint32_t)(PM_CLS(j) == U) << j;
+                            const uint32_t kmask = (1u << K2) - 1u;
+                            uint2 d2[4];
+                            uint32_t bits2 = 0;  // 5 bits per position: its code's bit in the word
+                            uint32_t dm = 0;
+#pragma unroll
+                            for (int q = 0; q < 4; ++q) {
+                                if (!((need >> q) & 1u) || lp0 + q + K2 > rel_end) continue;
+                                if ((om >> q) & kmask) {
+                                    need &= ~(1u << q);
+                                    continue;
+                                }
+                                uint32_t cc = 0;
+#pragma unroll
+                                for (int j = 0; j < (int)kDeepMaxK; ++j)
+                                    if (j < (int)K2) cc = cc * U + PM_CLS(q + j);
+                                if (MODE == MODE_CHECKED && (cc >> 5) >= t.deep_words) {
+                                    record_error(PM_ERR_BOUNDS);
+                                    need &= ~(1u << q);
+                                    continue;
+                                }
+                                bits2 |= (cc & 31u) << (5 * q);
+                                d2[q] = ld_trie_u2(t.deep + (cc >> 5), tpol);
+                                dm |= 1u << q;
+                            }
+#pragma unroll
+                            for (int q = 0; q < 4; ++q) {
+                                if (!((dm >> q) & 1u)) continue;
+                                const uint32_t bit = (bits2 >> (5 * q)) & 31u;
+                                if ((d2[q].x >> bit) & 1u)
+                                    rk[q] = d2[q].y + __popc(d2[q].x & ((1u << bit) - 1u));
+                                else
+                                    need &= ~(1u << q);
+                            }
+                            deepm = dm & need;
+                        }
+#undef PM_CLS
+                    }
+                    if (IDENT && KF >= 1 && need) {
+                        // byte alphabet: the depth-k node of each flagged
+                        // position (its k-gram's code, first byte most
+                        // significant); a k-gram that is not a root path
+                        // (a Bloom false positive) needs no walk
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            if (!((need >> q) & 1u)) continue;
+                            const uint32_t x = q == 0 ? w0 : __funnelshift_r(w0, w1, 8 * q);
+                            const uint32_t code = KF == 1 ? (x & 0xFFu) : __byte_perm(x, 0u, 0x4401u);
+                            if (MODE == MODE_CHECKED && (code >> 5) >= p.dense_u4 * 2) {
+                                record_error(PM_ERR_BOUNDS);
+                                need &= ~(1u << q);
                                 continue;
                             }
-                            need |= ((s_filt[word] >> (idx & 31u)) & 1u) << q;
+                            const uint2 d = s_dense[code >> 5];
+                            const uint32_t bit = code & 31u;
+                            if ((d.x >> bit) & 1u)
+                                rk[q] = d.y + __popc(d.x & ((1u << bit) - 1u));
+                            else
+                                need &= ~(1u << q);
                         }
                     }
                 } else {
@@ -731,36 +836,57 @@ __global__ void __launch_bounds__(1024, 1) pfac_scan_kernel(const KParams p)
                     for (int q = 0; q < 4; ++q)
                         if (lp0 + q < tile_n) __stcs(idt + lp0 + q, -1);
                 }
-                // warp ballot/popc compaction of the groups with work into
-                // the shared ring; the group's bytes travel with it
+                // warp ballot/popc compaction of the walks into the shared
+                // ring, one entry per walk (position, start depth, node)
                 const uint32_t work = need | rootm;
                 const uint32_t mg = __ballot_sync(0xffffffffu, work != 0);
                 if (mg) {
+                    // slots: walks ordered by position within the group, then
+                    // by lane; with at most one walk per lane (the common case
+                    // under a selective filter) one ballot gives them all
+                    uint32_t mq[4], off[4], tot = 0;
+                    if (!__any_sync(0xffffffffu, (work & (work - 1u)) != 0)) {
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            mq[q] = mg;
+                            off[q] = 0;
+                        }
+                        tot = __popc(mg);
+                    } else {
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            mq[q] = __ballot_sync(0xffffffffu, (work >> q) & 1u);
+                            off[q] = tot;
+                            tot += __popc(mq[q]);
+                        }
+                    }
                     uint32_t base = 0;
-                    if (lane == 0) base = atomicAdd(&ring->wr, (unsigned)__popc(mg));
+                    if (lane == 0) base = atomicAdd(&ring->wr, tot);
                     base = __shfl_sync(0xffffffffu, base, 0);
-                    if (work) {
-                        const uint32_t slot = base + __popc(mg & ((1u << lane) - 1u));
+                    const uint32_t below = (1u << lane) - 1u;
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        if (!((work >> q) & 1u) || failed) continue;
+                        const uint32_t slot = base + off[q] + __popc(mq[q] & below);
                         const uint32_t idx = slot & (kRing - 1);
                         const long long w0c = clock64();
-                        bool free_slot = true;
                         while (vf[idx] != slot) {  // until the cell is free for this slot
                             if (clock64() - w0c > kWaitBudget) {
                                 record_error(PM_ERR_TIMEOUT);
-                                free_slot = false;
+                                failed = true;
                                 break;
                             }
                         }
-                        if (free_slot) {
-                            const unsigned long long g0 = t0 + lp0;
-                            entries[idx] = make_uint4((uint32_t)g0,
-                                                      (uint32_t)(g0 >> 32) | (work << 24) | (rootm << 28),
-                                                      w0, w1);
-                            __threadfence_block();  // the -1 store and the entry before the flag
-                            vf[idx] = slot + 1u;
-                        } else {
-                            failed = true;
-                        }
+                        if (failed) break;
+                        const bool root = (rootm >> q) & 1u;
+                        const bool dp = (deepm >> q) & 1u;
+                        const uint32_t depth = root ? 0u : dp ? t.deep_k : k;
+                        const uint32_t node = root || depth == 0 ? 0u
+                                              : (dp ? t.deep_first : p.first_k) + rk[q];
+                        entries[idx] = walk_entry_of(t0 + lp0 + q, depth, node,
+                                                     BATCH && !root ? cur0 : 0xFFFFFFFFu);
+                        __threadfence_block();  // the -1 store and the entry before the flag
+                        vf[idx] = slot + 1u;
                     }
                     failed = __any_sync(0xffffffffu, failed);
                     if (failed) break;
@@ -937,6 +1063,11 @@ int launch_scan(const TrieDev &t, const pm_config &cfg, const ScanArgs &a, void 
     p.filter = t.filter[cfg.dense_k][width_index(cfg.filter_bits)];
     p.dense = cfg.dense_k > 0 ? t.dense[cfg.dense_k] : nullptr;
     p.first_k = t.first[cfg.dense_k];
+    p.ck1 = 1u;
+    for (int32_t i = 1; i < cfg.dense_k; ++i) p.ck1 *= t.C;
+    p.deep_on = cfg.deep && t.deep_k > 0 && t.C != 256 ? 1u : 0u;
+    p.kload = (uint32_t)cfg.dense_k + 4u;
+    if (p.deep_on && t.deep_k + 4u > p.kload) p.kload = t.deep_k + 4u;
     p.gram = t.gram[cfg.dense_k];
     p.binary = cfg.row_search ? 1u : 0u;
     p.stages = (uint32_t)cfg.stages;

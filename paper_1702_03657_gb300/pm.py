@@ -56,7 +56,8 @@ class pm_trie_stats(C.Structure):
         ("alphabet", C.c_uint32), ("dense_k_max", C.c_uint32),
         ("crs_elements", C.c_uint64), ("csr_bytes", C.c_uint64),
         ("dense256_bytes", C.c_uint64), ("bitmap36_bytes", C.c_uint64),
-        ("device_bytes", C.c_uint64),
+        ("device_bytes", C.c_uint64), ("deep_bytes", C.c_uint64),
+        ("deep_k", C.c_uint32),
     ]
 
     def as_dict(self):
@@ -81,7 +82,7 @@ class pm_server_stats(C.Structure):
 class pm_config(C.Structure):
     _fields_ = [(f, C.c_int32) for f in (
         "threads", "tile", "dense_k", "filter_bits", "row_search",
-        "ctas_per_sm", "stages", "checked", "walkers")]
+        "ctas_per_sm", "stages", "checked", "walkers", "deep")]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

@@ -24,13 +24,20 @@ def candidates(trie: pm.Trie, total_bytes: int) -> List[dict]:
     kmax = st["dense_k_max"]
     ks = sorted({kmax, max(kmax - 1, 0)})
     out = []
-    for threads, tile, stages, k, bits, walkers in itertools.product(
-            (1024, 512), (1024, 2048, 4096), (2, 3), ks, (8, 16, 32), (2, 4, 8)):
-        if walkers >= threads // 32:
+    for threads, tile, stages, k, bits, share in itertools.product(
+            (1024, 512), (1024, 2048, 4096), (2, 3), ks, (8, 16, 32),
+            ("2", "4", "8", "1/4", "1/2", "7/8")):
+        # walker warps: a few (selective filters) up to most of the CTA
+        # (tries whose filter passes most positions, e.g. DNA alphabets)
+        warps = threads // 32
+        walkers = int(share) if "/" not in share else \
+            warps * int(share[0]) // int(share[2])
+        if walkers >= warps or (share == "8" and walkers in (warps // 2, warps // 4)) or \
+                (share == "4" and walkers == warps // 4):
             continue
         c = dict(base, threads=threads, tile=tile, stages=stages, dense_k=k,
                  filter_bits=bits, row_search=0, checked=0, ctas_per_sm=0,
-                 walkers=walkers)
+                 walkers=walkers, deep=1 if st["deep_k"] else 0)
         try:
             pm.pm_set_config(trie, c)  # validates (shared memory, filter exists)
         except pm.PMError:

@@ -109,6 +109,39 @@ def test_classes_and_dense_levels(lib):
     assert pm.pm_stats(t)["alphabet"] == 256
 
 
+def _deep_words(U, d):
+    w = -(-U ** d // 32)
+    return w + (w & 1)
+
+
+def test_deep_level_selection(lib):
+    """The deep level: byte classes only, depth D2 in [K + 2, min_len - 1],
+    at most depth 13 and 2^26 codes over the used classes; a bitmap with a
+    rank word per 32 codes (8 bytes)."""
+    rng = np.random.Generator(np.random.MT19937(1))
+
+    def pats(alpha, lo, hi, n):
+        return [rng.choice(list(alpha), size=int(rng.integers(lo, hi + 1))).astype(np.uint8).tobytes()
+                for _ in range(n)]
+    # 4 letters, shortest 12: C = 5, K = 7 (5^7 <= 2^17), D2 = 11
+    st = pm.pm_stats(pm.pm_build_host(pats(b"ACGT", 12, 24, 500)))
+    assert (st["alphabet"], st["dense_k_max"], st["deep_k"]) == (5, 7, 11)
+    assert st["deep_bytes"] == 8 * _deep_words(4, 11)
+    # 3 letters, shortest 14: C = 4, K = 8, D2 = 13 (the window's limit)
+    st = pm.pm_stats(pm.pm_build_host(pats(b"xyz", 14, 20, 300)))
+    assert (st["dense_k_max"], st["deep_k"]) == (8, 13)
+    assert st["deep_bytes"] == 8 * _deep_words(3, 13)
+    # 26 letters, shortest 8: C = 27, K = 3, D2 = 5 (26^6 > 2^26)
+    st = pm.pm_stats(pm.pm_build_host(pats(b"abcdefghijklmnopqrstuvwxyz", 8, 16, 500)))
+    assert (st["dense_k_max"], st["deep_k"]) == (3, 5)
+    assert st["deep_bytes"] == 8 * _deep_words(26, 5)
+    # shortest pattern too close to K, and the byte alphabet: none
+    st = pm.pm_stats(pm.pm_build_host(pats(b"ACGT", 8, 12, 200)))
+    assert st["deep_k"] == 0 and st["deep_bytes"] == 0
+    st = pm.pm_stats(pm.pm_build_host([bytes(range(256))] + pats(bytes(range(256)), 20, 30, 50)))
+    assert st["alphabet"] == 256 and st["deep_k"] == 0
+
+
 def test_empty_set_and_host_only_scan(lib):
     t = pm.pm_build_host([])
     st = pm.pm_stats(t)
@@ -128,7 +161,7 @@ def test_config_validation(lib):
     assert cfg["threads"] in (128, 256, 512, 1024) and cfg["tile"] % 128 == 0
     pm.pm_set_config(t, cfg)
     for bad in ({"threads": 100}, {"tile": 1000}, {"dense_k": -1}, {"stages": 9},
-                {"dense_k": 99}, {"filter_bits": 12}):
+                {"dense_k": 99}, {"filter_bits": 12}, {"deep": 1}, {"deep": 2}):
         c = dict(cfg, **bad)
         with pytest.raises(pm.PMError) as e:
             pm.pm_set_config(t, c)

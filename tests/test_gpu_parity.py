@@ -183,6 +183,48 @@ def test_degenerate_pattern_sets():
         assert look == o_look
 
 
+@pytest.mark.parametrize("seed,alphabet,npat,lo,hi,deep_k", [
+    (20, 4, 3000, 12, 24, 11), (21, 3, 800, 14, 20, 13), (22, 26, 2000, 8, 16, 5),
+])
+def test_deep_level(seed, alphabet, npat, lo, hi, deep_k):
+    """Byte-class tries whose shortest pattern lies well below the shared-memory
+    levels get a deep level in L2. With it on and off, checked and counting
+    lookups, and with bytes outside the patterns' alphabet in the text, the
+    bits equal the oracle's; a batch of short texts (shorter than the deep
+    level's depth) too."""
+    wl = W.random_case(seed, npat, 150_001, alphabet, lo, hi, plant_rate=0.05)
+    rng = np.random.Generator(np.random.MT19937(seed))
+    text = wl.text.copy()
+    other = rng.random(len(text)) < 0.002           # bytes on no trie edge
+    text[other] = ord("Z")
+    t = pm.pm_build(wl.patterns)
+    st = pm.pm_stats(t)
+    assert st["deep_k"] == deep_k
+    assert st["deep_bytes"] > 0
+    cfg = pm.pm_get_config(t)
+    assert cfg["deep"] == 1
+    ot = oracle.Trie(wl.patterns)
+    o_ids, o_cnt, o_look = ot.scan(text)
+    assert o_cnt > 0
+    for c in (None, dict(cfg, deep=0), dict(cfg, checked=1), small_cfg(t),
+              small_cfg(t, deep=0, dense_k=1), dict(cfg, tile=128, stages=4)):
+        ids, cnt, _ = gpu_scan(t, text, cfg=c)
+        assert_same(ids, cnt, o_ids, o_cnt)
+    _, _, look = gpu_scan(t, text, lookups=True)
+    assert look == o_look
+    # batch: texts around the deep level's depth
+    pieces, a = [], 0
+    for n in [0, 1, deep_k - 1, deep_k, deep_k + 1, 3, 100, 5000, deep_k + 3, 2]:
+        pieces.append(text[a:a + n])
+        a += n + 7
+    data, off = W.concat(pieces)
+    bw = W.Workload("deep_batch", seed, wl.patterns, data, off)
+    b_ids, b_counts, _ = ot.scan_batch(data, off)
+    for c in (None, small_cfg(t), dict(cfg, deep=0)):
+        ids, counts = batch_gpu(t, bw, c)
+        assert np.array_equal(ids, b_ids) and np.array_equal(counts, b_counts)
+
+
 def test_tiny_config_full():
     wl = W.tiny(0)
     t = pm.pm_build(wl.patterns)
