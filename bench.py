@@ -7,6 +7,12 @@ outputs resident in HBM. The metric is Gbps of text scanned (8 * bytes /
 time), with the kernel's roofline fraction beside it.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+                  [--workload paper|acgt|tiny]
+
+The default workload is the paper-scale one; ``--workload acgt`` (100,000
+patterns of 20-32 bytes over ACGT, 1 GiB text, 1 % planted) and ``tiny``
+(100 patterns over 'a'-'z', 1 MiB) time the other plain configurations in
+the same way, without the batched and serving legs.
 
 Under torchrun each rank scans its own text (weak scaling, no data-path
 collective); the step time is the max over ranks. ``--impl reference`` times
@@ -33,8 +39,23 @@ METRIC = "Gbps scanned & % roofline, batched/served vs plain PFAC (bit-exact); p
 WORKLOAD = ("paper-scale plain PFAC: 20,000 patterns over bytes 0-255, lengths 8-64, "
             "p=0.5 shared prefix with an earlier pattern; 256 MiB uniform text, "
             "1 planted pattern per 64 KiB; seed 0")
-TEXT_BYTES = 256 * 1024 * 1024
 N_PATTERNS = 20000
+WORKLOADS = {
+    "paper": (WORKLOAD, 256),
+    "acgt": ("dense small alphabet plain PFAC: 100,000 patterns over ACGT, lengths 20-32; "
+             "{mib} MiB i.i.d. uniform ACGT text, 1 % of positions start a planted "
+             "pattern; seed 0", 1024),
+    "tiny": ("tiny plain PFAC: 100 patterns over 'a'-'z', lengths 4-16; {mib} MiB text "
+             "over 'a'-'z', one planted pattern per 4 KiB; seed 0", 1),
+}
+
+
+def make_workload(W, name: str, seed: int, mib: int):
+    if name == "acgt":
+        return W.acgt(seed, text_bytes=mib << 20)
+    if name == "tiny":
+        return W.tiny(seed, text_bytes=mib << 20)
+    return W.paper_scale(seed, text_bytes=mib << 20, n_patterns=N_PATTERNS)
 
 
 def parse():
@@ -49,7 +70,8 @@ def parse():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--serving-requests", type=int, default=10000)
-    ap.add_argument("--text-mib", type=int, default=256,
+    ap.add_argument("--workload", default="paper", choices=sorted(WORKLOADS))
+    ap.add_argument("--text-mib", type=int, default=None,
                     help="text size (the metric is quoted at 256; smaller sizes "
                          "are for profiler captures)")
     return ap.parse_args()
@@ -121,10 +143,13 @@ def kernel_source_sha():
     return h.hexdigest()
 
 
-def profiled_traffic():
-    """DRAM bytes per launch from the committed ncu summary, if it was taken
-    on the current kernel source (else None)."""
-    path = os.path.join(ROOT, "profiles", "pfac_scan_paper_scale.md")
+def profiled_traffic(workload: str = "paper"):
+    """DRAM bytes per launch from the committed ncu summary of the workload,
+    if it was taken on the current kernel source (else None)."""
+    name = {"paper": "pfac_scan_paper_scale.md", "acgt": "pfac_scan_acgt.md"}.get(workload)
+    if name is None:
+        return None
+    path = os.path.join(ROOT, "profiles", name)
     try:
         txt = open(path).read()
     except OSError:
@@ -144,7 +169,41 @@ def measured_peak_hbm():
         return 6800.0, "fallback"
 
 
-def cpu_baseline(wl, seconds: float):
+L2_METHOD = ("torch copy between two L2-resident 40 MiB buffers, 50 copies per CUDA "
+             "graph, read + write bytes over CUDA-event time, best of 5 replays")
+
+
+def measured_l2_gbs(torch):
+    """L2 bandwidth for the trie term (see L2_METHOD); no driver-measured
+    figure exists for it."""
+    a = torch.empty(40 << 20, dtype=torch.uint8, device="cuda")
+    b = torch.empty_like(a)
+    a.fill_(1)
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        for _ in range(5):
+            b.copy_(a)
+    torch.cuda.current_stream().wait_stream(s)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        for _ in range(50):
+            b.copy_(a)
+    g.replay()
+    torch.cuda.synchronize()
+    best = 0.0
+    for _ in range(5):
+        e0, e1 = torch.cuda.Event(True), torch.cuda.Event(True)
+        e0.record()
+        g.replay()
+        e1.record()
+        torch.cuda.synchronize()
+        best = max(best, 2 * a.numel() * 50 / (e0.elapsed_time(e1) / 1e3) / 1e9)
+    del g
+    return round(best, 1)
+
+
+def cpu_baseline(wl, seconds: float, name: str = "256 MiB paper-scale"):
     """The oracle's PFAC walk, as it stands, on the host cores, over a
     bounded contiguous sample of the same text."""
     import oracle
@@ -160,7 +219,7 @@ def cpu_baseline(wl, seconds: float):
     dt = time.perf_counter() - t0
     return {"value": round(8 * n / dt / 1e9, 4), "unit": "Gbps", "cores": cores,
             "kind": "oracle",
-            "sample": f"start positions 0..{n} of the 256 MiB paper-scale text "
+            "sample": f"start positions 0..{n} of the {name} text "
                       f"({n / len(wl.text) * 100:.2f}%), PFAC pointer-trie walk, "
                       f"{cores} threads, {dt:.1f} s"}
 
@@ -317,7 +376,9 @@ def run_reference(args, rank, world):
         return
     from paper_1702_03657_gb300 import workloads as W
     import oracle
-    wl = W.paper_scale(0, text_bytes=TEXT_BYTES, n_patterns=N_PATTERNS)
+    desc, def_mib = WORKLOADS[args.workload]
+    mib = args.text_mib or def_mib
+    wl = make_workload(W, args.workload, 0, mib)
     cores = os.cpu_count() or 1
     t = oracle.Trie(wl.patterns)
     probe = 1 << 18
@@ -336,12 +397,13 @@ def run_reference(args, rank, world):
     dt = time.perf_counter() - t0
     value = 8 * per_step * args.steps / dt / 1e9
     sample = (f"{per_step} consecutive start positions per step at seeded random offsets "
-              f"of the 256 MiB paper-scale text; PFAC pointer-trie walk on {cores} threads")
+              f"of the {mib} MiB {args.workload} text; PFAC pointer-trie walk on "
+              f"{cores} threads")
     line = {"impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": "Gbps",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": round(dt / args.steps * 1e3, 4), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "sample_positions_per_step": per_step},
+            "config": {"workload": desc.format(mib=mib), "sample_positions_per_step": per_step},
             "cpu_baseline": {"value": round(value, 4), "unit": "Gbps", "cores": cores,
                              "kind": "oracle", "sample": sample},
             "e2e": {"value": round(value, 4), "unit": "Gbps", "h2d_bytes_per_step": 0,
@@ -368,7 +430,9 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     pm.load()
 
-    wl = W.paper_scale(rank, text_bytes=args.text_mib << 20, n_patterns=N_PATTERNS)
+    desc, def_mib = WORKLOADS[args.workload]
+    mib = args.text_mib or def_mib
+    wl = make_workload(W, args.workload, rank, mib)
     trie = pm.pm_build(wl.patterns)
     stats = pm.pm_stats(trie)
     cfg = pm.pm_get_config(trie)
@@ -379,8 +443,8 @@ def main():
     stream = torch.cuda.current_stream()
 
     # trie-lookup count (instrumented kernel, outside the timed region) on
-    # the first 4 MiB of the text, scaled to the whole text
-    look_n = min(n, 4 << 20)
+    # the first 1 MiB of the text, scaled to the whole text
+    look_n = min(n, 1 << 20)
     look = torch.zeros(1, dtype=torch.int64, device="cuda")
     pm.pm_scan_ex(trie, text, None, ids, cnt, lookups=look, length=look_n)
     torch.cuda.synchronize()
@@ -416,7 +480,16 @@ def main():
     alg_bytes = n + 4 * n + 8                   # text read + int32 ids + count
     achieved = alg_bytes / avg_launch_s / 1e9   # GB/s
     peak, peak_kind = measured_peak_hbm()
-    traffic = profiled_traffic()
+    traffic = profiled_traffic(args.workload) if mib == def_mib else None
+    # trie term: 4 bytes per transition the oracle attempts, at L2 bandwidth
+    # the oracle's root walks need lookups; the kernel's dense levels, filter
+    # and deep level skip most of them, so the HBM term is the one its
+    # traffic follows (the roofline object); both terms are reported
+    l2 = measured_l2_gbs(torch)
+    trie_bytes = 4 * lookups
+    t_hbm, t_trie = alg_bytes / (peak * 1e9), trie_bytes / (l2 * 1e9)
+    roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+            "frac": round(achieved / peak, 4), "traffic": traffic, "peak_kind": peak_kind}
 
     # end to end through the C ABI with host buffers (pm_scan_host)
     h_text = torch.from_numpy(wl.text).pin_memory()
@@ -445,33 +518,44 @@ def main():
         return
     cpu = None
     if not args.no_cpu_baseline and world == 1:
-        cpu = cpu_baseline(wl, args.cpu_seconds)
-    batched = None if args.no_batched else bench_batched(pm, W, torch, reps=200)
-    serving = None if args.no_serving else bench_serving(pm, W, torch, args.serving_requests)
+        cpu = cpu_baseline(wl, args.cpu_seconds, f"{mib} MiB {args.workload}")
+    other = args.workload != "paper"
+    batched = None if args.no_batched or other else bench_batched(pm, W, torch, reps=200)
+    serving = None if args.no_serving or other else \
+        bench_serving(pm, W, torch, args.serving_requests)
     line = {
         "metric": METRIC, "value": round(gbps, 2), "unit": "Gbps", "n_gpus": world,
         "steps": K, "warmup": args.warmup, "ms_per_step": round(total_ms / K, 5),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "text_bytes": n, "patterns": N_PATTERNS,
-                   "launch": cfg, "l2": "inputs larger than L2 (256 MiB text + 1 GiB ids "
-                                        "per step), no flush",
+        "config": {"workload": desc.format(mib=mib), "text_bytes": n,
+                   "patterns": int(stats["n_patterns"]),
+                   "launch": cfg,
+                   "l2": (f"inputs larger than L2 ({mib} MiB text + {4 * mib} MiB ids per "
+                          "step), no flush") if 5 * mib > 126 else
+                         f"inputs ({5 * mib} MiB) fit in L2: not a roofline claim",
                    "parallelism": f"text sharded per rank x{world} (independent texts)"},
-        "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
-                     "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": traffic,
-                     "peak_kind": peak_kind,
+        "roofline": dict(roof, **{
                      "algorithmic_bytes_per_launch": alg_bytes,
+                     "hbm_term": {"bytes": alg_bytes, "peak_gbs": peak,
+                                  "bound_ms": round(t_hbm * 1e3, 4)},
                      "trie_term": {"lookups": lookups,
                                    "lookups_per_byte": round(lookups / n, 4),
-                                   "bytes": 4 * lookups,
-                                   "sample": f"counted on the first {look_n} bytes, scaled"}},
+                                   "bytes": trie_bytes, "l2_gbs": l2, "l2_method": L2_METHOD,
+                                   "bound_ms": round(t_trie * 1e3, 4),
+                                   "sample": f"counted on the first {look_n} bytes, scaled"},
+                     "two_term": {"binding": "hbm" if t_hbm >= t_trie else "trie",
+                                  "frac_of_time": round(max(t_hbm, t_trie) / avg_launch_s, 4),
+                                  "rule": "max(hbm bytes / HBM peak, 4 B x oracle lookups / "
+                                          "L2 bandwidth) / kernel time"}}),
         "e2e": e2e,
         "gpu_launches": K,
         "clocks": clocks.summary(),
         "cpu_baseline": cpu,
         "trie": {k: stats[k] for k in ("n_nodes", "nnz", "csr_bytes", "dense256_bytes",
                                        "bitmap36_bytes", "crs_elements", "alphabet",
-                                       "dense_k_max")},
+                                       "dense_k_max", "deep_k", "deep_bytes",
+                                       "device_bytes")},
         "matches": count,
         "batched": batched,
         "serving": serving,
