@@ -16,6 +16,10 @@ Both return ``(ids int32[n], count, lookups)`` where ``ids[i]`` is the id of
 the longest pattern occurring at start position i (-1 if none), ``count`` the
 number of (position, pattern) occurrences and ``lookups`` the number of trie
 transitions attempted.
+
+The all-matches form, ``naive_all`` and ``Trie.scan_all``, returns every
+occurrence as ``(pos int64[m], id int32[m], length int32[m])`` ordered by
+position, then the longer pattern first.
 """
 from __future__ import annotations
 
@@ -70,6 +74,10 @@ def _load():
     lib.otrie_degrees.restype = None
     lib.oracle_pfac.argtypes = [P, P, i64, i64, i64, P, P, P]
     lib.oracle_pfac.restype = None
+    lib.oracle_naive_all.argtypes = [P, P, i32, P, i64, i64, i64, P, P, P, i64, P]
+    lib.oracle_naive_all.restype = _C.c_int
+    lib.oracle_pfac_all.argtypes = [P, P, i64, i64, i64, P, P, P, i64, P]
+    lib.oracle_pfac_all.restype = _C.c_int
     _lib = lib
     return lib
 
@@ -111,6 +119,31 @@ def naive(patterns, text, i0: int = 0, i1: int = None):
     if rc != 0:
         raise ValueError("empty pattern")
     return ids, cnt.value, look.value
+
+
+def _all_calls(call):
+    """Run an all-matches oracle call twice: count, then fill."""
+    n = _C.c_int64(0)
+    if call(None, None, None, 0, _C.byref(n)) != 0:
+        raise ValueError("empty pattern or out of memory")
+    m = n.value
+    pos = np.empty(m, dtype=np.int64)
+    ids = np.empty(m, dtype=np.int32)
+    lens = np.empty(m, dtype=np.int32)
+    if m and call(pos.ctypes.data, ids.ctypes.data, lens.ctypes.data, m, _C.byref(n)) != 0:
+        raise ValueError("out of memory")
+    return pos, ids, lens
+
+
+def naive_all(patterns, text, i0: int = 0, i1: int = None):
+    """Every occurrence by the definition, over start positions [i0, i1)."""
+    lib = _load()
+    data, off = _pack(patterns)
+    t = _text(text)
+    n = len(t)
+    i1 = n if i1 is None else i1
+    return _all_calls(lambda p, d, l, cap, nn: lib.oracle_naive_all(
+        data.ctypes.data, off.ctypes.data, len(off) - 1, _ptr(t), n, i0, i1, p, d, l, cap, nn))
 
 
 class Trie:
@@ -180,6 +213,28 @@ class Trie:
             with _cf.ThreadPoolExecutor(threads) as ex:
                 res = list(ex.map(part, range(threads)))
         return ids, sum(r[0] for r in res), sum(r[1] for r in res)
+
+    def scan_all(self, text, i0: int = 0, i1: int = None, threads: int = 1):
+        """Every occurrence by the PFAC walk over start positions [i0, i1),
+        split over ``threads`` contiguous ranges."""
+        t = _text(text)
+        n = len(t)
+        i1 = n if i1 is None else i1
+        m = max(i1 - i0, 0)
+        threads = max(1, min(threads, m // 4096 + 1))
+        bounds = [i0 + (m * k) // threads for k in range(threads + 1)]
+
+        def part(k):
+            a, b = bounds[k], bounds[k + 1]
+            return _all_calls(lambda p, d, l, cap, nn: self._lib.oracle_pfac_all(
+                self._h, _ptr(t), n, a, b, p, d, l, cap, nn))
+
+        if threads == 1:
+            res = [part(0)]
+        else:
+            with _cf.ThreadPoolExecutor(threads) as ex:
+                res = list(ex.map(part, range(threads)))
+        return tuple(np.concatenate([r[j] for r in res]) for j in range(3))
 
     def scan_batch(self, text, offsets, threads: int = 1):
         """Scan each text text[offsets[k]:offsets[k+1]] on its own (no match

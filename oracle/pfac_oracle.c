@@ -25,6 +25,12 @@
  *                 inserting one pattern at a time (trie construction, step I
  *                 of Section III; numbering is irrelevant to the outputs).
  *
+ * The all-matches form (every occurrence, not only the longest per position;
+ * Sections II-B and II-C ask for all matches) lists each (position, pattern
+ * id, pattern length) in the order: position ascending, then the longer
+ * pattern first. oracle_naive_all and oracle_pfac_all compute it the same two
+ * independent ways.
+ *
  * Plain C99, no threads; callers split position ranges across threads.
  */
 #include <stdint.h>
@@ -73,6 +79,55 @@ int oracle_naive(const uint8_t *pat, const int64_t *off, int32_t npat,
     }
     if (count) *count = cnt;
     if (lookups) *lookups = look;
+    return 0;
+}
+
+/* Every occurrence over start positions [i0, i1), by the definition: the
+ * distinct patterns occurring at each position, sorted longest first (two
+ * patterns occurring at one position are prefixes of each other, so their
+ * lengths differ). Writes entries k < cap of pos/id/plen and returns the
+ * number of occurrences in *n; -1 for an empty pattern or out of memory. */
+int oracle_naive_all(const uint8_t *pat, const int64_t *off, int32_t npat,
+                     const uint8_t *text, int64_t len, int64_t i0, int64_t i1,
+                     int64_t *pos, int32_t *id, int32_t *plen, int64_t cap, int64_t *n)
+{
+    int64_t k = 0;
+    int32_t *hit = malloc(sizeof(int32_t) * (size_t)(npat > 0 ? npat : 1));
+    if (!hit) return -1;
+    for (int32_t j = 0; j < npat; ++j)
+        if (off[j + 1] <= off[j]) {
+            free(hit);
+            return -1;
+        }
+    for (int64_t i = i0; i < i1; ++i) {
+        int32_t nh = 0;
+        for (int32_t j = 0; j < npat; ++j) {
+            const uint8_t *p = pat + off[j];
+            int64_t L = off[j + 1] - off[j];
+            if (i + L > len || memcmp(text + i, p, (size_t)L) != 0) continue;
+            int dup = 0;
+            for (int32_t q = 0; q < j && !dup; ++q) {
+                int64_t Lq = off[q + 1] - off[q];
+                dup = (Lq == L) && memcmp(pat + off[q], p, (size_t)L) == 0;
+            }
+            if (dup) continue;
+            /* insert keeping lengths descending */
+            int32_t a = nh++;
+            while (a > 0 && off[hit[a - 1] + 1] - off[hit[a - 1]] < L) {
+                hit[a] = hit[a - 1];
+                --a;
+            }
+            hit[a] = j;
+        }
+        for (int32_t a = 0; a < nh; ++a, ++k) {
+            if (k >= cap) continue;
+            pos[k] = i;
+            id[k] = hit[a];
+            plen[k] = (int32_t)(off[hit[a] + 1] - off[hit[a]]);
+        }
+    }
+    free(hit);
+    *n = k;
     return 0;
 }
 
@@ -217,4 +272,46 @@ void oracle_pfac(const otrie *t, const uint8_t *text, int64_t len,
     }
     if (count) *count = cnt;
     if (lookups) *lookups = look;
+}
+
+/* Every occurrence over start positions [i0, i1) by the PFAC walk: the final
+ * nodes a walk passes are the patterns occurring at its start, shallowest
+ * first; they are listed deepest first. Same output contract as
+ * oracle_naive_all; returns -1 when out of memory. */
+int oracle_pfac_all(const otrie *t, const uint8_t *text, int64_t len, int64_t i0, int64_t i1,
+                    int64_t *pos, int32_t *id, int32_t *plen, int64_t cap, int64_t *n)
+{
+    int64_t k = 0;
+    int32_t *fid = malloc(sizeof(int32_t) * (size_t)(t->max_len + 1));
+    int32_t *fl = malloc(sizeof(int32_t) * (size_t)(t->max_len + 1));
+    if (!fid || !fl) {
+        free(fid);
+        free(fl);
+        return -1;
+    }
+    for (int64_t i = i0; i < i1; ++i) {
+        int32_t v = 0, nf = 0;
+        int64_t j = i;
+        while (j < len) {
+            int32_t c = child_of(t, v, text[j]);
+            if (c < 0) break;
+            v = c;
+            ++j;
+            if (t->nodes[v].final_id >= 0) {
+                fid[nf] = t->nodes[v].final_id;
+                fl[nf] = (int32_t)(j - i);
+                ++nf;
+            }
+        }
+        for (int32_t a = nf - 1; a >= 0; --a, ++k) {
+            if (k >= cap) continue;
+            pos[k] = i;
+            id[k] = fid[a];
+            plen[k] = fl[a];
+        }
+    }
+    free(fid);
+    free(fl);
+    *n = k;
+    return 0;
 }

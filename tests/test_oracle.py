@@ -73,6 +73,15 @@ def both(pats, text):
     return a, b
 
 
+def both_all(pats, text):
+    """The all-matches form by the definition and by the walk, as lists of
+    [position, id, length]."""
+    out = []
+    for pos, ids, lens in (oracle.naive_all(pats, text), oracle.Trie(pats).scan_all(text)):
+        out.append([[int(a), int(b), int(c)] for a, b, c in zip(pos, ids, lens)])
+    return out
+
+
 @pytest.mark.parametrize("case", _fixtures())
 def test_golden(case):
     a, b = both(case["patterns"], case["text"])
@@ -80,6 +89,67 @@ def test_golden(case):
         assert ids.tolist() == case["ids"]
         assert cnt == case["count"]
         assert look == case["lookups"]
+    for got in both_all(case["patterns"], case["text"]):
+        assert got == case["matches"]
+        assert len(got) == case["count"]
+
+
+@pytest.mark.parametrize("m,n", [(1, 1), (3, 4), (5, 3), (7, 40)])
+def test_all_matches_closed_form_unary(m, n):
+    """P = {a, ..., a^m}, T = a^n: at position i the patterns a^L with
+    L = min(m, n-i) down to 1 occur, a^L having id L-1."""
+    pats = [b"a" * k for k in range(1, m + 1)]
+    exp = [[i, L - 1, L] for i in range(n) for L in range(min(m, n - i), 0, -1)]
+    for got in both_all(pats, b"a" * n):
+        assert got == exp
+
+
+def py_brute_all(pats, text):
+    """Every occurrence by slicing, in plain Python: distinct patterns keep
+    their first index; per position the longer pattern first."""
+    first = {}
+    for j, p in enumerate(pats):
+        first.setdefault(p, j)
+    out = []
+    for i in range(len(text)):
+        hits = sorted((p for p in first if text[i:i + len(p)] == p), key=len, reverse=True)
+        out.extend([i, first[p], len(p)] for p in hits)
+    return out
+
+
+@pytest.mark.parametrize("seed,alphabet,npat,lo,hi", [
+    (0, 2, 12, 1, 6), (1, 3, 30, 1, 5), (3, 26, 50, 1, 4), (5, 256, 50, 1, 3),
+])
+def test_all_matches_against_python_brute_force(seed, alphabet, npat, lo, hi):
+    wl = W.random_case(seed, npat, 1200, alphabet, lo, hi, plant_rate=0.08)
+    pats = wl.patterns.as_list()
+    pats = pats + [pats[0], pats[len(pats) // 2][:1]]
+    text = wl.text.tobytes()
+    exp = py_brute_all(pats, text)
+    for got in both_all(pats, text):
+        assert got == exp
+
+
+def test_all_matches_agree_with_scan():
+    """The longest-first list starts every matched position with ids[i], has
+    count entries, and each entry is an occurrence; thread splits agree."""
+    wl = W.random_case(8, 200, 30000, 3, 1, 9, plant_rate=0.1)
+    t = oracle.Trie(wl.patterns)
+    ids, cnt, _ = t.scan(wl.text)
+    pos, mid, lens = t.scan_all(wl.text)
+    assert len(pos) == cnt
+    assert np.all(np.diff(pos) >= 0)
+    text = wl.text.tobytes()
+    pats = wl.patterns.as_list()
+    firsts = np.r_[True, pos[1:] != pos[:-1]]
+    assert np.array_equal(mid[firsts], ids[pos[firsts]])
+    assert np.array_equal(np.unique(pos), np.flatnonzero(ids >= 0))
+    same = ~firsts
+    assert np.all(lens[same] < lens[np.flatnonzero(same) - 1])
+    for a, b, c in zip(pos[::97], mid[::97], lens[::97]):
+        assert len(pats[b]) == c and text[a:a + c] == pats[b]
+    p4 = t.scan_all(wl.text, threads=4)
+    assert all(np.array_equal(x, y) for x, y in zip((pos, mid, lens), p4))
 
 
 @pytest.mark.parametrize("m,n", [(1, 1), (3, 4), (5, 3), (7, 40), (40, 7)])
@@ -208,7 +278,7 @@ MUTATIONS = [
     # a walk that reached a final node must be counted
     ("                ++cnt;\n                best =", "                best ="),
     # the definition must count a repeated pattern once
-    ("if (dup) continue;", ""),
+    ("                if (dup) continue;\n                ++cnt;", "                ++cnt;"),
     # the definition must prefer the longer pattern
     ("if (L > best_len)", "if (best < 0)"),
     # no lookup is attempted once the text has ended
@@ -253,6 +323,58 @@ def _run_mutant(lib, pats, text):
                     C.byref(cnt), C.byref(look))
     res.append((ids[:n].tolist(), cnt.value, look.value))
     return res
+
+
+MUTATIONS_ALL = [
+    # the walk lists its finals deepest first, not in walk order
+    ("for (int32_t a = nf - 1; a >= 0; --a, ++k)", "for (int32_t a = 0; a < nf; ++a, ++k)"),
+    # a final's length is the bytes matched from the start
+    ("fl[nf] = (int32_t)(j - i);", "fl[nf] = (int32_t)(j - i - 1);"),
+    # the definition sorts each position's patterns longest first
+    ("off[hit[a - 1] + 1] - off[hit[a - 1]] < L", "off[hit[a - 1] + 1] - off[hit[a - 1]] > L"),
+    # the definition lists a repeated pattern once
+    ("            if (dup) continue;\n            /* insert", "            /* insert"),
+]
+
+
+@pytest.mark.parametrize("k", range(len(MUTATIONS_ALL)))
+def test_all_matches_mutations_are_caught(tmp_path, k):
+    """A slip planted in a copy of the all-matches oracle (on the CPU) makes
+    at least one hand-worked fixture's match list differ."""
+    import ctypes as C
+    src = open(oracle._SRC).read()
+    old, new = MUTATIONS_ALL[k]
+    assert src.count(old) == 1, old
+    lib = _load_mutant(tmp_path, src.replace(old, new))
+    P, i64, i32 = C.c_void_p, C.c_int64, C.c_int32
+    lib.oracle_naive_all.argtypes = [P, P, i32, P, i64, i64, i64, P, P, P, i64, P]
+    lib.oracle_pfac_all.argtypes = [P, P, i64, i64, i64, P, P, P, i64, P]
+    caught = False
+    for c in _fixtures():
+        case = c.values[0]
+        data, off = oracle._pack(case["patterns"])
+        text = bytes.fromhex(case["text"]) if isinstance(case["text"], str) else case["text"]
+        t = np.frombuffer(text + b"\0", np.uint8)
+        n = len(text)
+        cap = 64
+        pos, mid, lens = (np.zeros(cap, np.int64), np.zeros(cap, np.int32),
+                          np.zeros(cap, np.int32))
+        m = C.c_int64()
+        lib.oracle_naive_all(data.ctypes.data, off.ctypes.data, len(off) - 1, t.ctypes.data,
+                             n, 0, n, pos.ctypes.data, mid.ctypes.data, lens.ctypes.data,
+                             cap, C.byref(m))
+        got = [[int(a), int(b), int(c)] for a, b, c in
+               zip(pos[:m.value], mid[:m.value], lens[:m.value])]
+        caught |= got != case["matches"]
+        h = lib.otrie_new()
+        for j in range(len(off) - 1):
+            lib.otrie_insert(h, data.ctypes.data + int(off[j]), int(off[j + 1] - off[j]), j)
+        lib.oracle_pfac_all(h, t.ctypes.data, n, 0, n, pos.ctypes.data, mid.ctypes.data,
+                            lens.ctypes.data, cap, C.byref(m))
+        got = [[int(a), int(b), int(c)] for a, b, c in
+               zip(pos[:m.value], mid[:m.value], lens[:m.value])]
+        caught |= got != case["matches"]
+    assert caught, f"all-matches mutation {k} not caught"
 
 
 @pytest.mark.parametrize("k", range(len(MUTATIONS)))
