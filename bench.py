@@ -69,6 +69,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-all-matches", action="store_true")
     ap.add_argument("--serving-requests", type=int, default=10000)
     ap.add_argument("--workload", default="paper", choices=sorted(WORKLOADS))
     ap.add_argument("--text-mib", type=int, default=None,
@@ -512,6 +513,31 @@ def main():
            "api": "pm_scan_host (pinned host text in, host ids + count out)"}
     assert hc == count, "pm_scan_host count differs from pm_scan"
 
+    # every occurrence (pm_scan_all): the same scan plus the ordered list
+    all_matches = None
+    if not args.no_all_matches:
+        cap = count + 1024
+        mt = torch.empty((cap, 2), dtype=torch.int64, device="cuda")
+        work = torch.empty(pm.pm_scan_all_work_bytes(n), dtype=torch.uint8, device="cuda")
+        for _ in range(3):
+            pm.pm_scan_all(trie, text, ids, cnt, mt, work)
+        torch.cuda.synchronize()
+        Ka = max(1, min(K, 200))
+        e0, e1 = torch.cuda.Event(True), torch.cuda.Event(True)
+        e0.record(stream)
+        for _ in range(Ka):
+            pm.pm_scan_all(trie, text, ids, cnt, mt, work)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms_all = max_over_ranks(e0.elapsed_time(e1) / Ka, "cuda")
+        assert int(cnt.item()) == count, "pm_scan_all count differs from pm_scan"
+        all_matches = {"gbps": round(8.0 * n * world / (ms_all / 1e3) / 1e9, 2),
+                       "ms_per_step": round(ms_all, 5), "matches": count,
+                       "list_bytes": 16 * count, "steps": Ka,
+                       "overhead_vs_scan": round(ms_all / (total_ms / K) - 1.0, 4),
+                       "api": "pm_scan_all (ids + count + every occurrence, position "
+                              "order, longest first)"}
+
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
@@ -557,6 +583,7 @@ def main():
                                        "dense_k_max", "deep_k", "deep_bytes",
                                        "device_bytes")},
         "matches": count,
+        "all_matches": all_matches,
         "batched": batched,
         "serving": serving,
     }

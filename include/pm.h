@@ -182,6 +182,33 @@ int pm_scan_ex(const pm_trie *h, const uint8_t *d_texts,
                int32_t *d_ids, int64_t *d_counts, uint64_t *d_lookups,
                const pm_config *cfg, pm_stream stream);
 
+/* ---- all matches (Sections II-B and II-C: every occurrence) --------------
+ * One occurrence: pattern `id` (the index of its first occurrence in the
+ * pattern list) of `len` bytes occurs at text position `pos`. */
+typedef struct {
+    uint64_t pos;
+    int32_t id;
+    int32_t len;
+} pm_match;
+
+/* Bytes of device workspace pm_scan_all needs for a text of len bytes
+ * (a match count per 1024 positions plus two per 1 Mi positions). */
+uint64_t pm_scan_all_work_bytes(uint64_t len);
+
+/* pm_scan_all: pm_scan of one device text (out.ids and *out.count as
+ * there) plus every occurrence, written to d_matches[0 .. min(count,
+ * capacity)) ordered by position and, at one position, longer pattern first
+ * (the patterns occurring at a position are all prefixes of the longest).
+ * *out.count is the total; when it exceeds capacity the list stops after
+ * `capacity` entries (scan again with a larger buffer). d_work: caller-owned
+ * DEVICE workspace of at least pm_scan_all_work_bytes(len) bytes, 256-byte
+ * aligned, overwritten. Asynchronous on `stream`, no host synchronisation.
+ * Errors: PM_ERR_INVAL (null pointers, workspace too small or unaligned,
+ * len >= 2^40), PM_ERR_HOST_ONLY, PM_ERR_CUDA. */
+int pm_scan_all(const pm_trie *h, const uint8_t *d_text, uint64_t len, pm_result out,
+                pm_match *d_matches, uint64_t capacity, void *d_work, uint64_t work_bytes,
+                pm_stream stream);
+
 /* ---- host buffers ---------------------------------------------------------
  * pm_scan_host: scans a HOST text h_text[0..len) and returns the results in
  * host memory (h_ids int32[len], *h_count). The text is cut into chunks

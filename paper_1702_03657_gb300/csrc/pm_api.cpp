@@ -197,6 +197,7 @@ void fill_dev_sizes(pm_trie *h)
     d.deep_U = t.deep_U;
     d.deep_first = t.deep_first;
     d.deep_words = (uint32_t)(t.deep.size() / 2);
+    d.n_ids = (uint32_t)t.chain.size();
     for (int k = 0; k <= pm::kMaxDenseK; ++k) {
         d.dense_words[k] = (uint32_t)(t.dense[k].size() / 2);
         d.first[k] = t.first[k];
@@ -241,6 +242,9 @@ int upload(pm_trie *h)
     size_t i_emit = add(emit.data(), 8 * n);
     size_t i_cls = add(t.cls, 256);
     const size_t i_deep = t.deep.empty() ? (size_t)-1 : add(t.deep.data(), 4 * t.deep.size());
+    std::vector<int4> minfo(t.chain.size());
+    for (size_t i = 0; i < minfo.size(); ++i) minfo[i] = make_int4(t.chain[i], t.plen[i], t.mcnt[i], 0);
+    const size_t i_minfo = minfo.empty() ? (size_t)-1 : add(minfo.data(), 16 * minfo.size());
     const size_t none = (size_t)-1;
     size_t i_dense[pm::kMaxDenseK + 1];
     size_t i_f[pm::kMaxDenseK + 1][pm::kFilterWidths];
@@ -274,6 +278,7 @@ int upload(pm_trie *h)
     d.emit = reinterpret_cast<const int2 *>(base + parts[i_emit].off);
     d.cls = base + parts[i_cls].off;
     d.deep = i_deep == (size_t)-1 ? nullptr : reinterpret_cast<const uint2 *>(base + parts[i_deep].off);
+    d.minfo = i_minfo == (size_t)-1 ? nullptr : reinterpret_cast<const int4 *>(base + parts[i_minfo].off);
     for (int k = 0; k <= pm::kMaxDenseK; ++k) {
         d.dense[k] = i_dense[k] == none ? nullptr
                                         : reinterpret_cast<const uint2 *>(base + parts[i_dense[k]].off);
@@ -321,7 +326,8 @@ int build_common(const uint8_t *const *patterns, const uint32_t *lengths, uint32
 
 int scan_common(const pm_trie *h, const uint8_t *d_texts, const uint64_t *d_offsets,
                 uint32_t ntexts, uint64_t len, uint64_t limit, int32_t *d_ids, int64_t *d_counts,
-                uint64_t *d_lookups, const pm_config *cfg, pm_stream stream)
+                uint64_t *d_lookups, const pm_config *cfg, pm_stream stream,
+                uint32_t *tile_counts = nullptr)
 {
     if (!h) return fail(PM_ERR_INVAL, "handle is NULL");
     if (!h->d_arena) return fail(PM_ERR_HOST_ONLY, "handle was built with pm_build_host");
@@ -349,6 +355,7 @@ int scan_common(const pm_trie *h, const uint8_t *d_texts, const uint64_t *d_offs
     a.ids = d_ids;
     a.counts = d_counts;
     a.lookups = reinterpret_cast<unsigned long long *>(d_lookups);
+    a.tile_counts = tile_counts;
     std::string msg;
     int rc = pm::launch_scan(h->dev, c, a, stream, h->sms, msg);
     if (rc != PM_OK) return fail(rc, msg);
@@ -452,6 +459,34 @@ int pm_scan(const pm_trie *h, const uint8_t *d_text, uint64_t len, pm_result out
 {
     return scan_common(h, d_text, nullptr, 1, len, len, out.ids, out.count, nullptr, nullptr,
                        stream);
+}
+
+uint64_t pm_scan_all_work_bytes(uint64_t len) { return pm::match_work_bytes(len); }
+
+int pm_scan_all(const pm_trie *h, const uint8_t *d_text, uint64_t len, pm_result out,
+                pm_match *d_matches, uint64_t capacity, void *d_work, uint64_t work_bytes,
+                pm_stream stream)
+{
+    if (!h) return fail(PM_ERR_INVAL, "handle is NULL");
+    if (capacity > 0 && !d_matches) return fail(PM_ERR_INVAL, "matches is NULL with capacity > 0");
+    if (len >= (1ull << 40)) return fail(PM_ERR_INVAL, "text of 2^40 bytes or more");
+    const uint64_t need = pm::match_work_bytes(len);
+    if (len > 0 && (!d_work || work_bytes < need))
+        return fail(PM_ERR_INVAL, "workspace of " + std::to_string(need) + " bytes needed");
+    if (((uintptr_t)d_work & 255u) != 0) return fail(PM_ERR_INVAL, "workspace not 256-byte aligned");
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    const uint64_t ntiles = (len + (1ull << pm::kMatchTileShift) - 1) >> pm::kMatchTileShift;
+    if (len > 0 && h->d_arena) {
+        cudaError_t e = cudaMemsetAsync(d_work, 0, 4 * ntiles, st);
+        if (e != cudaSuccess) return cuda_fail("cudaMemsetAsync", e);
+    }
+    int rc = scan_common(h, d_text, nullptr, 1, len, len, out.ids, out.count, nullptr, nullptr,
+                         stream, len > 0 ? static_cast<uint32_t *>(d_work) : nullptr);
+    if (rc != PM_OK || len == 0) return rc;
+    std::string msg;
+    rc = pm::launch_matches(h->dev, out.ids, len, d_work, d_matches, capacity, stream, msg);
+    if (rc != PM_OK) return fail(rc, msg);
+    return ok();
 }
 
 int pm_scan_batch(const pm_trie *h, const uint8_t *d_texts, const uint64_t *d_offsets,

@@ -146,6 +146,9 @@ int build_host_trie(const uint8_t *const *patterns, const uint32_t *lengths,
     t.nfinal.clear();
     t.depth.clear();
     rng.push_back({0, m});
+    t.chain.assign(n, -1);
+    t.plen.assign(n, 0);
+    t.mcnt.assign(n, 0);
     t.final_id.push_back(-1);
     t.best.push_back(-1);
     t.nfinal.push_back(0);
@@ -167,6 +170,11 @@ int build_host_trie(const uint8_t *const *patterns, const uint32_t *lengths,
             int32_t fid = lengths[uq[k]] == d + 1 ? (int32_t)uq[k] : -1;
             t.final_id.push_back(fid);
             t.nfinal.push_back(t.nfinal[v] + (fid >= 0 ? 1 : 0));
+            if (fid >= 0) {
+                t.chain[fid] = t.best[v];  // deepest pattern strictly above
+                t.plen[fid] = (int32_t)(d + 1);
+                t.mcnt[fid] = t.nfinal.back();
+            }
             t.best.push_back(fid >= 0 ? fid : t.best[v]);
             t.depth.push_back(d + 1);
             k = e;

@@ -24,6 +24,8 @@ constexpr uint64_t kFilterBudget = 128u * 1024u;
 // from L2; at most 2^26 codes (16 MiB) and depth 13 (the producer's window).
 constexpr uint64_t kDeepCodes = 1ull << 26;
 constexpr uint32_t kDeepMaxK = 13;
+// All-matches: positions per tile of the match-count table.
+constexpr uint32_t kMatchTileShift = 10;
 // Filter widths: W = 8, 16, 32 bits per k-gram (index 0, 1, 2).
 constexpr int kFilterWidths = 3;
 
@@ -112,6 +114,8 @@ struct TrieDev {
     uint32_t deep_U;                                      // its code base: used classes
     uint32_t deep_first;                                  // BFS id of the first depth-deep_k node
     uint32_t deep_words;                                  // uint2 entries
+    const int4 *minfo;                                    // per pattern id (all-matches)
+    uint32_t n_ids;                                       // pattern id space (input count)
 };
 
 // Host-side trie: the CRS arrays plus the derived tables.
@@ -130,6 +134,10 @@ struct HostTrie {
     uint32_t dense_k_max = 0;
     uint32_t deep_k = 0, deep_U = 0, deep_first = 0;
     std::vector<uint32_t> deep;  // interleaved {bits, base} over deep_U^deep_k codes
+    // all-matches: per input pattern id (distinct patterns only, others -1/0):
+    // the next shorter pattern on its root path, its length, and the number
+    // of patterns on its root path (itself included)
+    std::vector<int32_t> chain, plen, mcnt;
     std::vector<uint32_t> dense[kMaxDenseK + 1];     // interleaved {bits, base}
     std::vector<uint32_t> filter[kMaxDenseK + 1][kFilterWidths];
     uint32_t first[kMaxDenseK + 1] = {};
@@ -161,7 +169,18 @@ struct ScanArgs {
     // batch only, optional: total text bytes when the host knows it (sizes
     // the persistent grid to the work; 0: one CTA per SM)
     uint64_t total_hint;
+    // single text only, optional: matches per tile of 2^kMatchTileShift
+    // start positions, added to (zeroed by the caller)
+    uint32_t *tile_counts;
 };
+
+// All-matches listing after a single-text scan with tile_counts (same
+// stream): lists every occurrence into out[0 .. capacity) in position order,
+// longest pattern first. work: the tile counts then the block sums and
+// offsets (match_work_bytes(len) bytes).
+uint64_t match_work_bytes(uint64_t len);
+int launch_matches(const TrieDev &t, const int32_t *ids, uint64_t len, void *work,
+                   pm_match *out, uint64_t capacity, void *stream, std::string &msg);
 
 // Enqueues the scan (counts zeroed first). Returns PM_OK / PM_ERR_CUDA.
 int launch_scan(const TrieDev &t, const pm_config &cfg, const ScanArgs &a,

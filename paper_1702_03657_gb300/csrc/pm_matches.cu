@@ -1,0 +1,196 @@
+// All-matches listing (Sections II-B and II-C ask for every occurrence of
+// every pattern): after a single-text scan has written the longest-match id
+// of every position and, per tile of 2^kMatchTileShift positions, the
+// number of occurrences starting there, three kernels list every occurrence
+// in position order, longest pattern first at a position:
+//   1. the match count of each block of kTilesPerBlock tiles;
+//   2. an exclusive scan of those block sums (one CTA);
+//   3. per block, an exclusive scan of its tile counts gives each tile's
+//      first output slot; warps take the tiles with matches, read their ids,
+//      and expand each matched position into the chain of patterns on its
+//      walk (the longest first, each pattern's next shorter one from the
+//      per-id table), at offsets from a warp scan.
+// The patterns occurring at a position are exactly the prefixes of its
+// longest match that are patterns, so the ids and the chains determine the
+// whole list.
+#include "pm_internal.h"
+
+namespace pm {
+namespace {
+
+constexpr uint32_t kTilesPerBlock = 1024;  // tiles per CTA of the listing kernels
+constexpr uint32_t kFull = 0xffffffffu;
+
+uint64_t round256(uint64_t x) { return (x + 255) & ~255ull; }
+
+__device__ __forceinline__ unsigned long long warp_inclusive_scan(unsigned long long x,
+                                                                  uint32_t lane)
+{
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long y = __shfl_up_sync(kFull, x, o);
+        if (lane >= (uint32_t)o) x += y;
+    }
+    return x;
+}
+
+// Block-wide exclusive scan of one value per thread (1024 threads); returns
+// the thread's exclusive prefix and sets *total.
+__device__ __forceinline__ unsigned long long block_exclusive_scan(unsigned long long v,
+                                                                   unsigned long long *ws,
+                                                                   unsigned long long *total)
+{
+    const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const unsigned long long x = warp_inclusive_scan(v, lane);
+    if (lane == 31) ws[warp] = x;
+    __syncthreads();
+    if (warp == 0) ws[lane] = warp_inclusive_scan(ws[lane], lane);
+    __syncthreads();
+    const unsigned long long pre = (warp ? ws[warp - 1] : 0ull) + x - v;
+    *total = ws[31];
+    __syncthreads();  // ws is reused by the caller's next scan
+    return pre;
+}
+
+__global__ void __launch_bounds__(1024, 1) pm_tile_sums_kernel(const uint32_t *tc,
+                                                               uint64_t ntiles,
+                                                               unsigned long long *bsum)
+{
+    __shared__ unsigned long long ws[32];
+    const uint64_t t = (uint64_t)blockIdx.x * kTilesPerBlock + threadIdx.x;
+    unsigned long long s = t < ntiles ? tc[t] : 0u;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(kFull, s, o);
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        s = ws[threadIdx.x];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(kFull, s, o);
+        if (threadIdx.x == 0) bsum[blockIdx.x] = s;
+    }
+}
+
+__global__ void __launch_bounds__(1024, 1) pm_block_scan_kernel(const unsigned long long *bsum,
+                                                                uint32_t nb,
+                                                                unsigned long long *boff)
+{
+    __shared__ unsigned long long ws[32];
+    unsigned long long carry = 0;
+    for (uint32_t base = 0; base < nb; base += blockDim.x) {
+        const uint32_t i = base + threadIdx.x;
+        const unsigned long long v = i < nb ? bsum[i] : 0ull;
+        unsigned long long tot;
+        const unsigned long long pre = block_exclusive_scan(v, ws, &tot);
+        if (i < nb) boff[i] = carry + pre;
+        carry += tot;
+    }
+}
+
+// One block of kTilesPerBlock tiles, one tile per thread for the scan of
+// the tile counts; then each warp lists its tiles with matches, each lane
+// 32 consecutive positions of the tile (read with 16-byte loads when the
+// ids are aligned), ordered across lanes by one warp scan of their record
+// counts.
+__global__ void __launch_bounds__(1024, 1) pm_matches_write_kernel(
+    const int32_t *ids, uint64_t len, const uint32_t *tc, uint64_t ntiles,
+    const unsigned long long *boff, const int4 *minfo, pm_match *out, uint64_t cap)
+{
+    __shared__ unsigned long long toff[kTilesPerBlock];
+    __shared__ uint32_t tcs[kTilesPerBlock];
+    __shared__ unsigned long long ws[32];
+    const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint64_t b0 = (uint64_t)blockIdx.x * kTilesPerBlock;
+    {
+        const uint64_t t = b0 + threadIdx.x;
+        const uint32_t c = t < ntiles ? tc[t] : 0u;
+        tcs[threadIdx.x] = c;
+        unsigned long long tot;
+        toff[threadIdx.x] = boff[blockIdx.x] + block_exclusive_scan(c, ws, &tot);
+    }
+    __syncthreads();
+    const bool vec = ((uintptr_t)ids & 15u) == 0;
+    for (uint32_t i = warp; i < kTilesPerBlock; i += 32) {
+        if (tcs[i] == 0) continue;
+        const uint64_t q0 = ((b0 + i) << kMatchTileShift) + 32ull * lane;  // lane's positions
+        int32_t v[32];
+        if (vec && q0 + 32 <= len) {
+            const int4 *src = reinterpret_cast<const int4 *>(ids + q0);
+#pragma unroll
+            for (int r = 0; r < 8; ++r) {
+                const int4 x = __ldg(src + r);
+                v[4 * r] = x.x;
+                v[4 * r + 1] = x.y;
+                v[4 * r + 2] = x.z;
+                v[4 * r + 3] = x.w;
+            }
+        } else {
+#pragma unroll
+            for (int r = 0; r < 32; ++r) v[r] = q0 + r < len ? __ldg(ids + q0 + r) : -1;
+        }
+        unsigned long long m = 0;
+#pragma unroll
+        for (int r = 0; r < 32; ++r)
+            if (v[r] >= 0) m += (unsigned long long)__ldg(&minfo[v[r]].z);
+        const unsigned long long x = warp_inclusive_scan(m, lane);
+        unsigned long long slot = toff[i] + x - m;
+        if (m == 0) continue;
+#pragma unroll
+        for (int r = 0; r < 32; ++r) {
+            if (v[r] < 0) continue;
+            // the position's patterns, longest first, down the chain
+            int32_t q = v[r];
+            int4 mi = __ldg(minfo + q);
+            const int32_t cnt = mi.z;
+            for (int32_t k = 0; k < cnt; ++k) {
+                if (slot < cap) {
+                    pm_match e;
+                    e.pos = q0 + r;
+                    e.id = q;
+                    e.len = mi.y;
+                    out[slot] = e;
+                }
+                ++slot;
+                if (k + 1 < cnt) {
+                    q = mi.x;  // next shorter pattern on the walk
+                    mi = __ldg(minfo + q);
+                }
+            }
+        }
+    }
+}
+
+}  // namespace
+
+uint64_t match_work_bytes(uint64_t len)
+{
+    const uint64_t ntiles = (len + (1ull << kMatchTileShift) - 1) >> kMatchTileShift;
+    const uint64_t nb = (ntiles + kTilesPerBlock - 1) / kTilesPerBlock;
+    return round256(4 * ntiles) + 2 * round256(8 * nb);
+}
+
+int launch_matches(const TrieDev &t, const int32_t *ids, uint64_t len, void *work,
+                   pm_match *out, uint64_t capacity, void *stream, std::string &msg)
+{
+    if (len == 0) return PM_OK;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    const uint64_t ntiles = (len + (1ull << kMatchTileShift) - 1) >> kMatchTileShift;
+    const uint64_t nb = (ntiles + kTilesPerBlock - 1) / kTilesPerBlock;
+    uint8_t *w = static_cast<uint8_t *>(work);
+    uint32_t *tc = reinterpret_cast<uint32_t *>(w);
+    unsigned long long *bsum = reinterpret_cast<unsigned long long *>(w + round256(4 * ntiles));
+    unsigned long long *boff =
+        reinterpret_cast<unsigned long long *>(w + round256(4 * ntiles) + round256(8 * nb));
+    pm_tile_sums_kernel<<<(unsigned)nb, 1024, 0, st>>>(tc, ntiles, bsum);
+    pm_block_scan_kernel<<<1, 1024, 0, st>>>(bsum, (uint32_t)nb, boff);
+    pm_matches_write_kernel<<<(unsigned)nb, 1024, 0, st>>>(ids, len, tc, ntiles, boff, t.minfo,
+                                                           out, capacity);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        msg = std::string("all-matches launch: ") + cudaGetErrorString(e);
+        return PM_ERR_CUDA;
+    }
+    return PM_OK;
+}
+
+}  // namespace pm

@@ -57,6 +57,7 @@ struct KParams {
     int32_t *const *out_ids;    // batch: per-text id buffers (nullptr: ids + offset)
     int64_t *counts;
     unsigned long long *lookups;
+    uint32_t *tile_counts;      // single text, optional: matches per position tile
     const uint32_t *filter;     // filter table of level k, width W (global)
     const uint2 *dense;         // dense table of level k (k >= 1, global)
     uint32_t first_k;           // BFS id of the first depth-k node
@@ -334,10 +335,12 @@ __device__ __forceinline__ void emit_walk(const KParams &p, unsigned long long p
         p.out_ids[txt][pos - __ldg(p.offsets + txt)] = em.x;
     else
         p.ids[pos] = em.x;
-    if (BATCH)
+    if (BATCH) {
         atomicAdd(reinterpret_cast<unsigned long long *>(p.counts + txt), (unsigned long long)em.y);
-    else
+    } else {
         acc += (unsigned)em.y;
+        if (p.tile_counts) atomicAdd(p.tile_counts + (pos >> kMatchTileShift), (unsigned)em.y);
+    }
 }
 
 // A ring entry is one walk: the start position (40 bits), the bytes already
@@ -1056,6 +1059,7 @@ int launch_scan(const TrieDev &t, const pm_config &cfg, const ScanArgs &a, void 
     p.out_ids = a.out_ids;
     p.counts = a.counts;
     p.lookups = a.lookups;
+    p.tile_counts = batch ? nullptr : a.tile_counts;
     p.tile = (uint32_t)cfg.tile;
     p.halo = L.halo;
     p.k = (uint32_t)cfg.dense_k;

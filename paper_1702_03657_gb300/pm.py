@@ -35,6 +35,7 @@ EXPORTS = (
     "pm_scan_host", "pm_scan_host_static", "pm_device_error", "pm_strerror", "pm_last_error",
     "pm_last_error_msg", "pm_server_create", "pm_submit", "pm_poll", "pm_wait",
     "pm_server_get_stats", "pm_server_destroy", "pm_server_replay", "pm_replay_plain",
+    "pm_scan_all", "pm_scan_all_work_bytes",
 )
 
 
@@ -133,6 +134,8 @@ def load(path: Optional[str] = None):
         "pm_server_destroy": ([P], C.c_int),
         "pm_server_replay": ([P, u32, P, P, P, P, P, P, P], C.c_int),
         "pm_replay_plain": ([P, u32, P, P, P, P, P, P, P, P, P], C.c_int),
+        "pm_scan_all": ([P, P, u64, pm_result, P, u64, P, u64, P], C.c_int),
+        "pm_scan_all_work_bytes": ([u64], u64),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -267,6 +270,39 @@ def pm_scan(trie: Trie, text, ids, count, stream=None, length: Optional[int] = N
     out = pm_result(_dptr(ids, torch.int32, "ids"), _dptr(count, torch.int64, "count"))
     _check(load().pm_scan(trie.handle, _dptr(text, torch.uint8, "text"), n, out,
                           _stream_ptr(stream)), "pm_scan")
+
+
+PM_MATCH_BYTES = 16  # pm_match: u64 pos, i32 id, i32 len
+
+
+def pm_scan_all_work_bytes(length: int) -> int:
+    return int(load().pm_scan_all_work_bytes(length))
+
+
+def pm_scan_all(trie: Trie, text, ids, count, matches, work, stream=None,
+                length: Optional[int] = None):
+    """pm_scan plus every occurrence: `matches` is an int64 CUDA tensor of
+    shape [capacity, 2] holding pm_match records (see decode_matches);
+    `work` a uint8 CUDA tensor of at least pm_scan_all_work_bytes(len)
+    bytes (torch allocations are 256-byte aligned)."""
+    import torch
+    n = text.numel() if length is None else length
+    if matches.dtype != torch.int64 or matches.dim() != 2 or matches.shape[1] != 2:
+        raise PMError(PM_ERR_INVAL, "matches", "must be an int64 tensor of shape [capacity, 2]")
+    out = pm_result(_dptr(ids, torch.int32, "ids"), _dptr(count, torch.int64, "count"))
+    _check(load().pm_scan_all(trie.handle, _dptr(text, torch.uint8, "text"), n, out,
+                              _dptr(matches, torch.int64, "matches"), matches.shape[0],
+                              _dptr(work, torch.uint8, "work"), work.numel(),
+                              _stream_ptr(stream)), "pm_scan_all")
+
+
+def decode_matches(matches, m: int):
+    """(pos int64[m], id int32[m], length int32[m]) from the first m pm_match
+    records of an int64 [capacity, 2] tensor."""
+    a = matches[:m].cpu().numpy()
+    hi = a[:, 1].view(np.uint64)
+    return (a[:, 0].copy(), (hi & 0xFFFFFFFF).astype(np.uint32).view(np.int32),
+            (hi >> 32).astype(np.uint32).view(np.int32))
 
 
 def pm_scan_batch(trie: Trie, texts, offsets, ids, counts, stream=None):

@@ -168,6 +168,25 @@ def test_config_validation(lib):
         assert e.value.code == pm.PM_ERR_INVAL
 
 
+def test_scan_all_host_side(lib):
+    """Workspace sizing (one u32 per 1024 positions, 256-byte aligned, plus
+    two u64 per 1024 tiles) and the errors that need no GPU."""
+    def r256(x):
+        return (x + 255) // 256 * 256
+    for n in (0, 1, 1024, 1025, 1024 * 1024, 1024 * 1024 + 1, 1 << 30):
+        tiles = -(-n // 1024)
+        blocks = -(-tiles // 1024)
+        assert pm.pm_scan_all_work_bytes(n) == r256(4 * tiles) + 2 * r256(8 * blocks)
+    import ctypes as C
+    t = pm.pm_build_host([b"abc"])
+    res = pm.pm_result(None, None)
+    assert lib.pm_scan_all(None, None, 0, res, None, 0, None, 0, None) == pm.PM_ERR_INVAL
+    cnt = C.c_int64()
+    res = pm.pm_result(None, C.addressof(cnt))
+    assert lib.pm_scan_all(t.handle, None, 0, res, None, 0, None, 0, None) == pm.PM_ERR_HOST_ONLY
+    assert lib.pm_scan_all(t.handle, None, 5, res, None, 0, None, 0, None) == pm.PM_ERR_INVAL
+
+
 def test_server_rejects_host_only_trie(lib):
     t = pm.pm_build_host([b"abc", b"abd"])
     with pytest.raises(pm.PMError) as e:
