@@ -70,6 +70,7 @@ def parse():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-all-matches", action="store_true")
+    ap.add_argument("--no-streaming", action="store_true")
     ap.add_argument("--serving-requests", type=int, default=10000)
     ap.add_argument("--workload", default="paper", choices=sorted(WORKLOADS))
     ap.add_argument("--text-mib", type=int, default=None,
@@ -538,6 +539,66 @@ def main():
                        "api": "pm_scan_all (ids + count + every occurrence, position "
                               "order, longest first)"}
 
+    # the same text as a stream of chunks (pm_scanner_*), device-resident
+    streaming = None
+    if not args.no_streaming:
+        streaming = []
+        H = max(int(stats["max_len"]) - 1, 0)
+        for chunk in (1 << 20, 64 << 10):
+            sc = pm.pm_scanner_open(trie)
+            sids = torch.empty(chunk + H + 1, dtype=torch.int32, device="cuda")
+            scnt = torch.empty(1, dtype=torch.int64, device="cuda")
+            acc = torch.zeros(1, dtype=torch.int64, device="cuda")
+
+            def one_stream():
+                for a in range(0, n, chunk):
+                    sc.push(text[a:a + chunk], sids, scnt)
+                    acc.add_(scnt)
+                sc.finish(sids, scnt)
+                acc.add_(scnt)
+            one_stream()
+            torch.cuda.synchronize()
+            acc.zero_()
+            reps = 3
+            e0, e1 = torch.cuda.Event(True), torch.cuda.Event(True)
+            e0.record(stream)
+            for _ in range(reps):
+                one_stream()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms_s = max_over_ranks(e0.elapsed_time(e1) / reps, "cuda")
+            ok_count = int(acc.item()) == reps * count
+            # the same stream captured once in a CUDA graph (device time
+            # without the Python loop; each replay starts from an empty carry)
+            g = torch.cuda.CUDAGraph()
+            gs = torch.cuda.Stream()
+            gs.wait_stream(torch.cuda.current_stream())
+            with torch.cuda.stream(gs):
+                with torch.cuda.graph(g, stream=gs):
+                    one_stream()
+            torch.cuda.current_stream().wait_stream(gs)
+            acc.zero_()
+            g.replay()
+            torch.cuda.synchronize()
+            ok_graph = int(acc.item()) == count
+            e0.record(stream)
+            for _ in range(reps):
+                g.replay()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms_g = max_over_ranks(e0.elapsed_time(e1) / reps, "cuda")
+            del g
+            streaming.append({"chunk_bytes": chunk, "pushes": (n + chunk - 1) // chunk,
+                              "gbps": round(8.0 * n * world / (ms_s / 1e3) / 1e9, 2),
+                              "ms_per_stream": round(ms_s, 4),
+                              "gbps_graph": round(8.0 * n * world / (ms_g / 1e3) / 1e9, 2),
+                              "ms_per_stream_graph": round(ms_g, 4),
+                              "count_equal": ok_count and ok_graph,
+                              "loop": "Python loop over pm_scanner_push; graph: the same "
+                                      "pushes captured once and replayed"})
+            sc.close()
+            assert ok_count and ok_graph, "streamed count differs from pm_scan"
+
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
@@ -584,6 +645,7 @@ def main():
                                        "device_bytes")},
         "matches": count,
         "all_matches": all_matches,
+        "streaming": streaming,
         "batched": batched,
         "serving": serving,
     }

@@ -209,6 +209,38 @@ int pm_scan_all(const pm_trie *h, const uint8_t *d_text, uint64_t len, pm_result
                 pm_match *d_matches, uint64_t capacity, void *d_work, uint64_t work_bytes,
                 pm_stream stream);
 
+/* ---- streams of chunks (Section II-B's overlap rule) ---------------------
+ * A scanner scans one long text that arrives in chunks (a packet or file
+ * stream) as if it were scanned whole. It holds back the last max_len - 1
+ * bytes of what it has seen (the carry) together with the start positions
+ * whose walks could still reach bytes not yet pushed.
+ *
+ * pm_scanner_push appends the DEVICE chunk d_chunk[0 .. len) and resolves
+ * every start position whose walk lies inside the bytes seen so far: all
+ * positions below (bytes pushed) - (max_len - 1), in stream order, starting
+ * with the held ones. Their ids go to d_ids[0 .. *n_ids) (d_ids holds at
+ * least len + max_len - 1 entries). *d_count is the number of occurrences
+ * among them, overwritten. *n_ids (HOST) is set before the call returns.
+ * The positions before a chunk boundary are scanned on a small copy of the
+ * carry and the chunk's first max_len - 1 bytes; the chunk's own positions
+ * are scanned in place.
+ * pm_scanner_finish ends the stream: the held positions are resolved with
+ * the stream's true end, and the scanner is ready for a new stream.
+ * Calls are asynchronous on `stream`. A scanner is used from one stream and
+ * one thread at a time; the chunk must stay valid until the push's work on
+ * the stream is done. Chunks up to 16 MiB are copied behind the carry into
+ * a scanner buffer and scanned in one launch; that buffer grows, stream
+ * ordered, to the largest such chunk. pm_scanner_close waits for the
+ * scanner's work on its last stream, then frees it.
+ * Errors: PM_ERR_INVAL, PM_ERR_HOST_ONLY (open), PM_ERR_NOMEM, PM_ERR_CUDA. */
+typedef struct pm_scanner pm_scanner;
+int pm_scanner_open(const pm_trie *h, pm_scanner **out);
+int pm_scanner_push(pm_scanner *s, const uint8_t *d_chunk, uint64_t len, int32_t *d_ids,
+                    int64_t *d_count, uint64_t *n_ids, pm_stream stream);
+int pm_scanner_finish(pm_scanner *s, int32_t *d_ids, int64_t *d_count, uint64_t *n_ids,
+                      pm_stream stream);
+int pm_scanner_close(pm_scanner *s);
+
 /* ---- host buffers ---------------------------------------------------------
  * pm_scan_host: scans a HOST text h_text[0..len) and returns the results in
  * host memory (h_ids int32[len], *h_count). The text is cut into chunks

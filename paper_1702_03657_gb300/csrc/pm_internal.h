@@ -172,6 +172,8 @@ struct ScanArgs {
     // single text only, optional: matches per tile of 2^kMatchTileShift
     // start positions, added to (zeroed by the caller)
     uint32_t *tile_counts;
+    // add to the counts instead of overwriting them
+    bool keep_counts;
 };
 
 // All-matches listing after a single-text scan with tile_counts (same

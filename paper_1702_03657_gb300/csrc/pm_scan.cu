@@ -30,6 +30,7 @@
 
 #include <atomic>
 #include <cstdio>
+#include <map>
 #include <mutex>
 
 #include "pm_internal.h"
@@ -1015,6 +1016,22 @@ Layout layout(const TrieDev &t, const pm_config &cfg)
 
 std::mutex g_attr_mu;
 
+struct LaunchKey {
+    const void *fn;
+    uint32_t smem, threads;
+    int device;
+    bool operator<(const LaunchKey &o) const
+    {
+        if (fn != o.fn) return fn < o.fn;
+        if (smem != o.smem) return smem < o.smem;
+        if (threads != o.threads) return threads < o.threads;
+        return device < o.device;
+    }
+};
+std::map<LaunchKey, int> g_occ;  // guarded by g_attr_mu
+// largest dynamic shared memory set per (kernel, device); only ever raised
+std::map<std::pair<const void *, int>, uint32_t> g_smem_set;  // guarded by g_attr_mu
+
 }  // namespace
 
 uint64_t scan_smem_bytes(const TrieDev &t, const pm_config &cfg)
@@ -1028,7 +1045,7 @@ int launch_scan(const TrieDev &t, const pm_config &cfg, const ScanArgs &a, void 
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     const bool batch = a.offsets != nullptr;
     const uint32_t ncount = batch ? a.ntexts : 1;
-    if (ncount) {
+    if (ncount && !a.keep_counts) {
         cudaError_t e = cudaMemsetAsync(a.counts, 0, sizeof(int64_t) * ncount, st);
         if (e != cudaSuccess) {
             msg = std::string("cudaMemsetAsync: ") + cudaGetErrorString(e);
@@ -1090,23 +1107,43 @@ int launch_scan(const TrieDev &t, const pm_config &cfg, const ScanArgs &a, void 
     p.filt_words = L.filt_words;
 
     cudaError_t e;
-    {
-        std::lock_guard<std::mutex> g(g_attr_mu);
-        e = cudaFuncSetAttribute(reinterpret_cast<const void *>(fn),
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total);
-    }
-    if (e != cudaSuccess) {
-        msg = std::string("shared memory ") + std::to_string(L.total) +
-              " bytes: " + cudaGetErrorString(e);
-        return PM_ERR_INVAL;
-    }
     int occ = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, reinterpret_cast<const void *>(fn),
-                                                      cfg.threads, L.total);
-    if (e != cudaSuccess || occ < 1) {
-        msg = "configuration does not fit on an SM (threads " + std::to_string(cfg.threads) +
-              ", shared " + std::to_string(L.total) + ")";
-        return PM_ERR_INVAL;
+    {
+        // the shared-memory attribute and the occupancy of each (kernel,
+        // shared bytes, threads, device) are set and queried once
+        int dev = -1;
+        e = cudaGetDevice(&dev);
+        if (e != cudaSuccess) {
+            msg = std::string("cudaGetDevice: ") + cudaGetErrorString(e);
+            return PM_ERR_CUDA;
+        }
+        const LaunchKey key{reinterpret_cast<const void *>(fn), L.total, (uint32_t)cfg.threads, dev};
+        std::lock_guard<std::mutex> g(g_attr_mu);
+        auto it = g_occ.find(key);
+        if (it != g_occ.end()) {
+            occ = it->second;
+        } else {
+            uint32_t &set = g_smem_set[{key.fn, dev}];
+            if (set < L.total) {
+                e = cudaFuncSetAttribute(reinterpret_cast<const void *>(fn),
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)L.total);
+                if (e != cudaSuccess) {
+                    msg = std::string("shared memory ") + std::to_string(L.total) +
+                          " bytes: " + cudaGetErrorString(e);
+                    return PM_ERR_INVAL;
+                }
+                set = L.total;
+            }
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                &occ, reinterpret_cast<const void *>(fn), cfg.threads, L.total);
+            if (e != cudaSuccess || occ < 1) {
+                msg = "configuration does not fit on an SM (threads " +
+                      std::to_string(cfg.threads) + ", shared " + std::to_string(L.total) + ")";
+                return PM_ERR_INVAL;
+            }
+            g_occ.emplace(key, occ);
+        }
     }
     if (cfg.ctas_per_sm > 0 && cfg.ctas_per_sm < occ) occ = cfg.ctas_per_sm;
     unsigned long long grid = (unsigned long long)device_sms * occ;

@@ -36,6 +36,7 @@ EXPORTS = (
     "pm_last_error_msg", "pm_server_create", "pm_submit", "pm_poll", "pm_wait",
     "pm_server_get_stats", "pm_server_destroy", "pm_server_replay", "pm_replay_plain",
     "pm_scan_all", "pm_scan_all_work_bytes",
+    "pm_scanner_open", "pm_scanner_push", "pm_scanner_finish", "pm_scanner_close",
 )
 
 
@@ -136,6 +137,10 @@ def load(path: Optional[str] = None):
         "pm_replay_plain": ([P, u32, P, P, P, P, P, P, P, P, P], C.c_int),
         "pm_scan_all": ([P, P, u64, pm_result, P, u64, P, u64, P], C.c_int),
         "pm_scan_all_work_bytes": ([u64], u64),
+        "pm_scanner_open": ([P, P], C.c_int),
+        "pm_scanner_push": ([P, P, u64, P, P, P, P], C.c_int),
+        "pm_scanner_finish": ([P, P, P, P, P], C.c_int),
+        "pm_scanner_close": ([P], C.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -303,6 +308,50 @@ def decode_matches(matches, m: int):
     hi = a[:, 1].view(np.uint64)
     return (a[:, 0].copy(), (hi & 0xFFFFFFFF).astype(np.uint32).view(np.int32),
             (hi >> 32).astype(np.uint32).view(np.int32))
+
+
+class Scanner:
+    """A stream of chunks scanned as one text (pm_scanner_*): each push
+    returns how many ids it wrote (the positions it resolved, in order)."""
+
+    def __init__(self, trie: Trie):
+        h = C.c_void_p()
+        _check(load().pm_scanner_open(trie.handle, C.byref(h)), "pm_scanner_open")
+        self.handle = h.value
+        self.trie = trie  # keeps the trie alive
+
+    def push(self, chunk, ids, count, stream=None, length: Optional[int] = None) -> int:
+        import torch
+        n = chunk.numel() if length is None else length
+        k = C.c_uint64()
+        _check(_lib.pm_scanner_push(self.handle, _dptr(chunk, torch.uint8, "chunk"), n,
+                                    _dptr(ids, torch.int32, "ids"),
+                                    _dptr(count, torch.int64, "count"), C.byref(k),
+                                    _stream_ptr(stream)), "pm_scanner_push")
+        return k.value
+
+    def finish(self, ids, count, stream=None) -> int:
+        import torch
+        k = C.c_uint64()
+        _check(_lib.pm_scanner_finish(self.handle, _dptr(ids, torch.int32, "ids"),
+                                      _dptr(count, torch.int64, "count"), C.byref(k),
+                                      _stream_ptr(stream)), "pm_scanner_finish")
+        return k.value
+
+    def close(self):
+        h, self.handle = self.handle, None
+        if h:
+            _check(_lib.pm_scanner_close(h), "pm_scanner_close")
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def pm_scanner_open(trie: Trie) -> Scanner:
+    return Scanner(trie)
 
 
 def pm_scan_batch(trie: Trie, texts, offsets, ids, counts, stream=None):

@@ -187,6 +187,17 @@ def test_scan_all_host_side(lib):
     assert lib.pm_scan_all(t.handle, None, 5, res, None, 0, None, 0, None) == pm.PM_ERR_INVAL
 
 
+def test_scanner_host_side(lib):
+    import ctypes as C
+    t = pm.pm_build_host([b"abc"])
+    h = C.c_void_p()
+    assert lib.pm_scanner_open(t.handle, C.byref(h)) == pm.PM_ERR_HOST_ONLY
+    assert lib.pm_scanner_open(None, C.byref(h)) == pm.PM_ERR_INVAL
+    assert lib.pm_scanner_push(None, None, 0, None, None, None, None) == pm.PM_ERR_INVAL
+    assert lib.pm_scanner_finish(None, None, None, None, None) == pm.PM_ERR_INVAL
+    assert lib.pm_scanner_close(None) == pm.PM_OK
+
+
 def test_server_rejects_host_only_trie(lib):
     t = pm.pm_build_host([b"abc", b"abd"])
     with pytest.raises(pm.PMError) as e:
