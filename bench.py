@@ -71,6 +71,7 @@ def parse():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-all-matches", action="store_true")
     ap.add_argument("--no-streaming", action="store_true")
+    ap.add_argument("--no-layouts", action="store_true")
     ap.add_argument("--serving-requests", type=int, default=10000)
     ap.add_argument("--workload", default="paper", choices=sorted(WORKLOADS))
     ap.add_argument("--text-mib", type=int, default=None,
@@ -514,6 +515,30 @@ def main():
            "api": "pm_scan_host (pinned host text in, host ids + count out)"}
     assert hc == count, "pm_scan_host count differs from pm_scan"
 
+    # the same scan with walks over the paper's bitmapped nodes (Section III:
+    # 256-bit child bitmap + first child, 36 bytes a node) instead of the
+    # 16-byte CRS row records
+    bitmap_nodes = None
+    if not args.no_layouts:
+        cfg_bm = dict(cfg, layout=1)
+        for _ in range(3):
+            pm.pm_scan_ex(trie, text, None, ids, cnt, cfg=cfg_bm)
+        torch.cuda.synchronize()
+        Kb = max(1, min(K, 200))
+        e0, e1 = torch.cuda.Event(True), torch.cuda.Event(True)
+        e0.record(stream)
+        for _ in range(Kb):
+            pm.pm_scan_ex(trie, text, None, ids, cnt, cfg=cfg_bm)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms_b = max_over_ranks(e0.elapsed_time(e1) / Kb, "cuda")
+        assert int(cnt.item()) == count, "bitmapped-node count differs"
+        nn = int(stats["n_nodes"])
+        bitmap_nodes = {"gbps": round(8.0 * n * world / (ms_b / 1e3) / 1e9, 2),
+                        "ms_per_step": round(ms_b, 5), "steps": Kb,
+                        "node_bytes": 36 * nn, "row_record_bytes": 16 * nn,
+                        "csr_bytes": int(stats["csr_bytes"])}
+
     # every occurrence (pm_scan_all): the same scan plus the ordered list
     all_matches = None
     if not args.no_all_matches:
@@ -645,6 +670,7 @@ def main():
                                        "device_bytes")},
         "matches": count,
         "all_matches": all_matches,
+        "bitmap_nodes": bitmap_nodes,
         "streaming": streaming,
         "batched": batched,
         "serving": serving,

@@ -109,6 +109,9 @@ typedef struct {
                           /* queue, 1 .. threads/32 - 1                       */
     int32_t deep;         /* 1: positions passing the filter look up the deep */
                           /* level before walking (needs deep_k > 0), 0: not */
+    int32_t layout;       /* trie form the walks read: 0 CRS row records (16  */
+                          /* bytes a node), 1 the bitmapped node of Section  */
+                          /* III (256-bit child bitmap + first child, 36 B)  */
 } pm_config;
 
 /* ---- trie construction (Section III, steps I, II, VI and the CRS step) --

@@ -85,6 +85,7 @@ pm_config default_config(const pm_trie *h, int smem_limit)
     c.stages = 2;
     c.checked = 0;
     c.deep = h->host.deep_k > 0 ? 1 : 0;
+    c.layout = 0;
     const uint64_t limit = (uint64_t)smem_limit - 1024;
     struct Pref {
         int32_t bits, tile;
@@ -170,6 +171,10 @@ int validate_config(const pm_trie *h, const pm_config &c, std::string &why)
         why = "row_search and checked are 0 or 1";
         return PM_ERR_INVAL;
     }
+    if (c.layout < 0 || c.layout > 1) {
+        why = "layout is 0 (CRS row records) or 1 (bitmapped nodes)";
+        return PM_ERR_INVAL;
+    }
     if (c.deep < 0 || c.deep > 1 || (c.deep == 1 && h->host.deep_k == 0)) {
         why = "deep is 0, or 1 when the trie has a deep level";
         return PM_ERR_INVAL;
@@ -245,6 +250,15 @@ int upload(pm_trie *h)
     std::vector<int4> minfo(t.chain.size());
     for (size_t i = 0; i < minfo.size(); ++i) minfo[i] = make_int4(t.chain[i], t.plen[i], t.mcnt[i], 0);
     const size_t i_minfo = minfo.empty() ? (size_t)-1 : add(minfo.data(), 16 * minfo.size());
+    // bitmapped nodes: 256-bit child bitmap + first child id per node
+    std::vector<uint32_t> bm(8 * n, 0), bm_first(n);
+    for (uint64_t v = 0; v < n; ++v) {
+        bm_first[v] = t.row_ptr[v] + 1;  // BFS: the child of non-zero e is node e + 1
+        for (uint32_t e = t.row_ptr[v]; e < t.row_ptr[v + 1]; ++e)
+            bm[8 * v + (t.col[e] >> 5)] |= 1u << (t.col[e] & 31);
+    }
+    const size_t i_bm = add(bm.data(), 32 * n);
+    const size_t i_bmf = add(bm_first.data(), 4 * n);
     const size_t none = (size_t)-1;
     size_t i_dense[pm::kMaxDenseK + 1];
     size_t i_f[pm::kMaxDenseK + 1][pm::kFilterWidths];
@@ -279,6 +293,8 @@ int upload(pm_trie *h)
     d.cls = base + parts[i_cls].off;
     d.deep = i_deep == (size_t)-1 ? nullptr : reinterpret_cast<const uint2 *>(base + parts[i_deep].off);
     d.minfo = i_minfo == (size_t)-1 ? nullptr : reinterpret_cast<const int4 *>(base + parts[i_minfo].off);
+    d.bm = reinterpret_cast<const uint4 *>(base + parts[i_bm].off);
+    d.bm_first = reinterpret_cast<const uint32_t *>(base + parts[i_bmf].off);
     for (int k = 0; k <= pm::kMaxDenseK; ++k) {
         d.dense[k] = i_dense[k] == none ? nullptr
                                         : reinterpret_cast<const uint2 *>(base + parts[i_dense[k]].off);

@@ -115,6 +115,11 @@ struct TrieDev {
     uint32_t deep_first;                                  // BFS id of the first depth-deep_k node
     uint32_t deep_words;                                  // uint2 entries
     const int4 *minfo;                                    // per pattern id (all-matches)
+    // Bitmapped nodes (Section III, Fig. 3): node v's children as a 256-bit
+    // bitmap over bytes (two uint4 at bm[2v]) and the id of its first child;
+    // the child on byte b is first + (set bits below b)
+    const uint4 *bm;
+    const uint32_t *bm_first;
     uint32_t n_ids;                                       // pattern id space (input count)
 };
 

@@ -71,6 +71,7 @@ struct KParams {
     uint32_t k;
     uint32_t lw;                // log2 W
     uint32_t binary;
+    uint32_t bitmap;            // walks read bitmapped nodes instead of row records
     uint32_t stages;
     uint32_t walkers;           // walker warps per CTA (the rest produce)
     uint32_t aligned;
@@ -381,6 +382,33 @@ __device__ __forceinline__ void run_walk(const KParams &p, uint4 e, unsigned lon
             return;
         }
         const uint32_t b = __ldg(tp + jo);
+        if (p.bitmap) {
+            // bitmapped node (Section III, Fig. 3): the child on byte b is
+            // first + (set bits below b) when bit b is set
+            const uint4 lo = ld_trie_u4(t.bm + 2 * (size_t)v, pol);
+            const uint4 hi = ld_trie_u4(t.bm + 2 * (size_t)v + 1, pol);
+            const uint32_t first = ld_trie_u32(t.bm_first + v, pol);
+            if (MODE == MODE_LOOKUPS) ++look;
+            const uint32_t w = b >> 5, bit = b & 31u;
+            uint32_t below = 0, hitw = 0;
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const uint32_t wi = i == 0 ? lo.x : i == 1 ? lo.y : i == 2 ? lo.z : i == 3 ? lo.w
+                                  : i == 4 ? hi.x : i == 5 ? hi.y : i == 6 ? hi.z : hi.w;
+                const uint32_t m = (uint32_t)i < w ? 0xFFFFFFFFu
+                                   : (uint32_t)i == w ? (1u << bit) - 1u : 0u;
+                below += __popc(wi & m);
+                if ((uint32_t)i == w) hitw = wi;
+            }
+            if (!((hitw >> bit) & 1u)) break;
+            if (MODE == MODE_CHECKED && first + below >= t.n_nodes) {
+                record_error(PM_ERR_BOUNDS);
+                return;
+            }
+            v = first + below;
+            ++jo;
+            continue;
+        }
         const uint4 r = ld_trie_u4(t.row + v, pol);
         const uint32_t deg = r.y & 0x1FFu;
         has = r.y >> 31;
@@ -1091,6 +1119,7 @@ int launch_scan(const TrieDev &t, const pm_config &cfg, const ScanArgs &a, void 
     if (p.deep_on && t.deep_k + 4u > p.kload) p.kload = t.deep_k + 4u;
     p.gram = t.gram[cfg.dense_k];
     p.binary = cfg.row_search ? 1u : 0u;
+    p.bitmap = cfg.layout == 1 ? 1u : 0u;
     p.stages = (uint32_t)cfg.stages;
     p.walkers = (uint32_t)cfg.walkers;
     p.aligned = ((uintptr_t)a.text & 15u) == 0;

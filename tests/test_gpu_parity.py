@@ -225,6 +225,33 @@ def test_deep_level(seed, alphabet, npat, lo, hi, deep_k):
         assert np.array_equal(ids, b_ids) and np.array_equal(counts, b_counts)
 
 
+def test_bitmapped_node_layout():
+    """Walks over the bitmapped nodes of Section III (256-bit child bitmap +
+    first child, child = first + rank) give the same bits as the CRS row
+    records: byte alphabets with long rows, small alphabets, a deep level,
+    checked, counting and batched."""
+    cases = [W.random_case(31, 500, 99_999, 256, 1, 8, plant_rate=0.05),
+             W.random_case(32, 300, 70_003, 3, 1, 9, plant_rate=0.05),
+             W.random_case(33, 2000, 120_001, 4, 12, 24, plant_rate=0.05),
+             W.paper_scale(3, text_bytes=2 * W.MiB + 3, n_patterns=3000)]
+    for wl in cases:
+        t = pm.pm_build(wl.patterns)
+        ot = oracle.Trie(wl.patterns)
+        o_ids, o_cnt, o_look = ot.scan(wl.text, threads=8)
+        base = pm.pm_get_config(t)
+        for c in (dict(base, layout=1), dict(base, layout=1, checked=1),
+                  small_cfg(t, layout=1, dense_k=0, deep=0)):
+            ids, cnt, _ = gpu_scan(t, wl.text, cfg=c)
+            assert_same(ids, cnt, o_ids, o_cnt)
+        _, _, look = gpu_scan(t, wl.text, cfg=dict(base, layout=1), lookups=True)
+        assert look == o_look
+    wl = W.batched(5, ntexts=300, n_patterns=3000)
+    t = pm.pm_build(wl.patterns)
+    o_ids, o_counts, _ = oracle.Trie(wl.patterns).scan_batch(wl.text, wl.offsets)
+    ids, counts = batch_gpu(t, wl, cfg=dict(pm.pm_get_config(t), layout=1))
+    assert np.array_equal(ids, o_ids) and np.array_equal(counts, o_counts)
+
+
 def test_tiny_config_full():
     wl = W.tiny(0)
     t = pm.pm_build(wl.patterns)
