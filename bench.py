@@ -539,6 +539,15 @@ def main():
                         "node_bytes": 36 * nn, "row_record_bytes": 16 * nn,
                         "csr_bytes": int(stats["csr_bytes"])}
 
+    # the truncated levels as an exact prefilter: walks queued vs positions
+    wk = torch.zeros(1, dtype=torch.int64, device="cuda")
+    pm.pm_scan_walks(trie, text, ids, cnt, wk)
+    torch.cuda.synchronize()
+    walks = int(wk.item())
+    prefilter = {"walks": walks, "walks_per_position": round(walks / max(n, 1), 6),
+                 "settled_without_walk": round(1.0 - walks / max(n, 1), 6),
+                 "matched_positions_walked": True}
+
     # every occurrence (pm_scan_all): the same scan plus the ordered list
     all_matches = None
     if not args.no_all_matches:
@@ -671,6 +680,7 @@ def main():
         "matches": count,
         "all_matches": all_matches,
         "bitmap_nodes": bitmap_nodes,
+        "prefilter": prefilter,
         "streaming": streaming,
         "batched": batched,
         "serving": serving,

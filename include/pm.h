@@ -185,6 +185,16 @@ int pm_scan_ex(const pm_trie *h, const uint8_t *d_texts,
                int32_t *d_ids, int64_t *d_counts, uint64_t *d_lookups,
                const pm_config *cfg, pm_stream stream);
 
+/* pm_scan_walks: pm_scan of one device text with an explicit configuration
+ * (NULL: the handle's) that also counts, into the DEVICE u64 *d_walks
+ * (overwritten), the walks it queued: the start positions the truncated
+ * levels (filter, dense tables, deep level) could not settle. Every other
+ * position was decided without a CRS walk.
+ * Errors: as pm_scan_ex. */
+int pm_scan_walks(const pm_trie *h, const uint8_t *d_text, uint64_t len, int32_t *d_ids,
+                  int64_t *d_count, uint64_t *d_walks, const pm_config *cfg,
+                  pm_stream stream);
+
 /* ---- all matches (Sections II-B and II-C: every occurrence) --------------
  * One occurrence: pattern `id` (the index of its first occurrence in the
  * pattern list) of `len` bytes occurs at text position `pos`. */

@@ -343,7 +343,7 @@ int build_common(const uint8_t *const *patterns, const uint32_t *lengths, uint32
 int scan_common(const pm_trie *h, const uint8_t *d_texts, const uint64_t *d_offsets,
                 uint32_t ntexts, uint64_t len, uint64_t limit, int32_t *d_ids, int64_t *d_counts,
                 uint64_t *d_lookups, const pm_config *cfg, pm_stream stream,
-                uint32_t *tile_counts = nullptr)
+                uint32_t *tile_counts = nullptr, uint64_t *d_walks = nullptr)
 {
     if (!h) return fail(PM_ERR_INVAL, "handle is NULL");
     if (!h->d_arena) return fail(PM_ERR_HOST_ONLY, "handle was built with pm_build_host");
@@ -372,6 +372,7 @@ int scan_common(const pm_trie *h, const uint8_t *d_texts, const uint64_t *d_offs
     a.counts = d_counts;
     a.lookups = reinterpret_cast<unsigned long long *>(d_lookups);
     a.tile_counts = tile_counts;
+    a.walks = reinterpret_cast<unsigned long long *>(d_walks);
     std::string msg;
     int rc = pm::launch_scan(h->dev, c, a, stream, h->sms, msg);
     if (rc != PM_OK) return fail(rc, msg);
@@ -475,6 +476,19 @@ int pm_scan(const pm_trie *h, const uint8_t *d_text, uint64_t len, pm_result out
 {
     return scan_common(h, d_text, nullptr, 1, len, len, out.ids, out.count, nullptr, nullptr,
                        stream);
+}
+
+int pm_scan_walks(const pm_trie *h, const uint8_t *d_text, uint64_t len, int32_t *d_ids,
+                  int64_t *d_count, uint64_t *d_walks, const pm_config *cfg, pm_stream stream)
+{
+    if (!d_walks) return fail(PM_ERR_INVAL, "walks is NULL");
+    if (h && h->d_arena) {
+        const cudaError_t e =
+            cudaMemsetAsync(d_walks, 0, sizeof(uint64_t), reinterpret_cast<cudaStream_t>(stream));
+        if (e != cudaSuccess) return cuda_fail("cudaMemsetAsync", e);
+    }
+    return scan_common(h, d_text, nullptr, 1, len, len, d_ids, d_count, nullptr, cfg, stream,
+                       nullptr, d_walks);
 }
 
 uint64_t pm_scan_all_work_bytes(uint64_t len) { return pm::match_work_bytes(len); }

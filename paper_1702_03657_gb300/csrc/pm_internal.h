@@ -179,6 +179,9 @@ struct ScanArgs {
     uint32_t *tile_counts;
     // add to the counts instead of overwriting them
     bool keep_counts;
+    // optional: number of walks queued (positions the filter, dense and deep
+    // levels could not settle), added to
+    unsigned long long *walks;
 };
 
 // All-matches listing after a single-text scan with tile_counts (same

@@ -59,6 +59,7 @@ struct KParams {
     int64_t *counts;
     unsigned long long *lookups;
     uint32_t *tile_counts;      // single text, optional: matches per position tile
+    unsigned long long *walks;  // optional: walks queued
     const uint32_t *filter;     // filter table of level k, width W (global)
     const uint2 *dense;         // dense table of level k (k >= 1, global)
     uint32_t first_k;           // BFS id of the first depth-k node
@@ -893,7 +894,10 @@ __global__ void __launch_bounds__(1024, 1) pfac_scan_kernel(const KParams p)
                         }
                     }
                     uint32_t base = 0;
-                    if (lane == 0) base = atomicAdd(&ring->wr, tot);
+                    if (lane == 0) {
+                        base = atomicAdd(&ring->wr, tot);
+                        if (p.walks) atomicAdd(p.walks, (unsigned long long)tot);
+                    }
                     base = __shfl_sync(0xffffffffu, base, 0);
                     const uint32_t below = (1u << lane) - 1u;
 #pragma unroll
@@ -1105,6 +1109,7 @@ int launch_scan(const TrieDev &t, const pm_config &cfg, const ScanArgs &a, void 
     p.counts = a.counts;
     p.lookups = a.lookups;
     p.tile_counts = batch ? nullptr : a.tile_counts;
+    p.walks = a.walks;
     p.tile = (uint32_t)cfg.tile;
     p.halo = L.halo;
     p.k = (uint32_t)cfg.dense_k;

@@ -35,7 +35,7 @@ EXPORTS = (
     "pm_scan_host", "pm_scan_host_static", "pm_device_error", "pm_strerror", "pm_last_error",
     "pm_last_error_msg", "pm_server_create", "pm_submit", "pm_poll", "pm_wait",
     "pm_server_get_stats", "pm_server_destroy", "pm_server_replay", "pm_replay_plain",
-    "pm_scan_all", "pm_scan_all_work_bytes",
+    "pm_scan_all", "pm_scan_all_work_bytes", "pm_scan_walks",
     "pm_scanner_open", "pm_scanner_push", "pm_scanner_finish", "pm_scanner_close",
 )
 
@@ -137,6 +137,7 @@ def load(path: Optional[str] = None):
         "pm_replay_plain": ([P, u32, P, P, P, P, P, P, P, P, P], C.c_int),
         "pm_scan_all": ([P, P, u64, pm_result, P, u64, P, u64, P], C.c_int),
         "pm_scan_all_work_bytes": ([u64], u64),
+        "pm_scan_walks": ([P, P, u64, P, P, P, P, P], C.c_int),
         "pm_scanner_open": ([P, P], C.c_int),
         "pm_scanner_push": ([P, P, u64, P, P, P, P], C.c_int),
         "pm_scanner_finish": ([P, P, P, P, P], C.c_int),
@@ -275,6 +276,19 @@ def pm_scan(trie: Trie, text, ids, count, stream=None, length: Optional[int] = N
     out = pm_result(_dptr(ids, torch.int32, "ids"), _dptr(count, torch.int64, "count"))
     _check(load().pm_scan(trie.handle, _dptr(text, torch.uint8, "text"), n, out,
                           _stream_ptr(stream)), "pm_scan")
+
+
+def pm_scan_walks(trie: Trie, text, ids, count, walks, cfg: Optional[dict] = None,
+                  stream=None, length: Optional[int] = None):
+    """pm_scan that also counts the walks queued into `walks` (int64[1])."""
+    import torch
+    n = text.numel() if length is None else length
+    c = pm_config.from_dict(cfg) if cfg is not None else None
+    _check(load().pm_scan_walks(trie.handle, _dptr(text, torch.uint8, "text"), n,
+                                _dptr(ids, torch.int32, "ids"), _dptr(count, torch.int64, "count"),
+                                _dptr(walks, torch.int64, "walks"),
+                                C.byref(c) if c is not None else None, _stream_ptr(stream)),
+           "pm_scan_walks")
 
 
 PM_MATCH_BYTES = 16  # pm_match: u64 pos, i32 id, i32 len

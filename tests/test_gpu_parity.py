@@ -252,6 +252,35 @@ def test_bitmapped_node_layout():
     assert np.array_equal(ids, o_ids) and np.array_equal(counts, o_counts)
 
 
+def walks_of(t, text, cfg=None):
+    tv = dev(text)
+    ids = torch.empty(len(text), dtype=torch.int32, device="cuda")
+    cnt = torch.empty(1, dtype=torch.int64, device="cuda")
+    wk = torch.full((1,), -1, dtype=torch.int64, device="cuda")
+    pm.pm_scan_walks(t, tv, ids, cnt, wk, cfg=cfg)
+    torch.cuda.synchronize()
+    return ids.cpu().numpy(), int(cnt.item()), int(wk.item())
+
+
+def test_truncated_levels_settle_positions():
+    """The filter, dense tables and deep level are the trie truncated at a
+    depth below the shortest pattern, used as an exact prefilter: every
+    matched position is walked (verified in the full trie), most others are
+    settled without a walk, and the bits are the oracle's either way."""
+    for wl, frac in ((W.paper_scale(1, text_bytes=6 * W.MiB + 1), 0.005),
+                     (W.acgt(1, text_bytes=4 * W.MiB + 7, n_patterns=100_000), 0.05)):
+        t = pm.pm_build(wl.patterns)
+        o_ids, o_cnt, _ = oracle.Trie(wl.patterns).scan(wl.text, threads=HOST_THREADS)
+        ids, cnt, walks = walks_of(t, wl.text)
+        assert_same(ids, cnt, o_ids, o_cnt)
+        matched = int((o_ids >= 0).sum())
+        assert matched <= walks <= frac * len(wl.text)
+        if pm.pm_stats(t)["deep_k"]:
+            ids0, cnt0, walks0 = walks_of(t, wl.text, cfg=dict(pm.pm_get_config(t), deep=0))
+            assert_same(ids0, cnt0, o_ids, o_cnt)
+            assert walks0 > 10 * walks
+
+
 def test_tiny_config_full():
     wl = W.tiny(0)
     t = pm.pm_build(wl.patterns)
