@@ -65,6 +65,7 @@ struct KParams {
     uint32_t first_k;           // BFS id of the first depth-k node
     uint32_t ck1;               // C^(k-1) (k >= 1): weight of a k-gram's first class
     uint32_t kload;             // byte classes: classes a group reads (k or deep_k, + 4)
+    uint32_t uk1;               // U^(deep_k - 1): weight of a deep gram's first class
     uint32_t deep_on;           // look up the deep level before walking
     uint32_t gram;              // bytes the filter tests per position (k+1 or k+2)
     uint32_t tile;
@@ -738,31 +739,47 @@ __global__ void __launch_bounds__(1024, 1) pfac_scan_kernel(const KParams p)
                             // (deep_k < shortest pattern); else the walk
                             // starts at depth deep_k.
                             const uint32_t K2 = t.deep_k, U = t.deep_U;
-                            uint32_t om = 0;  // bit j: the byte at lp0 + j is of the "other" class
+                            // bit j: the byte at lp0 + j is of the "other" class
+                            // (an exact zero-byte test of class xor U per word,
+                            // its four byte flags gathered by one multiply)
+                            uint32_t om = 0;
 #pragma unroll
-                            for (int j = 0; j < 16; ++j) om |= (uint32_t)(PM_CLS(j) == U) << j;
+                            for (int w = 0; w < 4; ++w) {
+                                const uint32_t x = cw[w] ^ (U * 0x01010101u);
+                                const uint32_t nz = ((x & 0x7F7F7F7Fu) + 0x7F7F7F7Fu) | x;
+                                const uint32_t zf = (~nz & 0x80808080u) >> 7;  // 1 per zero byte
+                                om |= (((zf * 0x00204081u) >> 21) & 0xFu) << (4 * w);
+                            }
                             const uint32_t kmask = (1u << K2) - 1u;
+                            // the first position's deep code by Horner's rule,
+                            // the next ones by rolling (classes K2 .. K2+2 enter)
+                            uint32_t cc = 0;
+#pragma unroll
+                            for (int j = 0; j < (int)kDeepMaxK; ++j)
+                                if (j < (int)K2) cc = cc * U + PM_CLS(j);
+                            const uint32_t kw2 = K2 >> 2;
+                            const uint32_t ea = kw2 == 0 ? cw[0] : kw2 == 1 ? cw[1] : kw2 == 2 ? cw[2] : cw[3];
+                            const uint32_t eb = kw2 == 0 ? cw[1] : kw2 == 1 ? cw[2] : cw[3];
+                            const uint32_t enter = __funnelshift_r(ea, eb, 8u * (K2 & 3u));
                             uint2 d2[4];
                             uint32_t bits2 = 0;  // 5 bits per position: its code's bit in the word
                             uint32_t dm = 0;
 #pragma unroll
                             for (int q = 0; q < 4; ++q) {
+                                const uint32_t cq = cc;
+                                if (q < 3) cc = (cc - PM_CLS(q) * p.uk1) * U + ((enter >> (8 * q)) & 0xFFu);
                                 if (!((need >> q) & 1u) || lp0 + q + K2 > rel_end) continue;
                                 if ((om >> q) & kmask) {
                                     need &= ~(1u << q);
                                     continue;
                                 }
-                                uint32_t cc = 0;
-#pragma unroll
-                                for (int j = 0; j < (int)kDeepMaxK; ++j)
-                                    if (j < (int)K2) cc = cc * U + PM_CLS(q + j);
-                                if (MODE == MODE_CHECKED && (cc >> 5) >= t.deep_words) {
+                                if (MODE == MODE_CHECKED && (cq >> 5) >= t.deep_words) {
                                     record_error(PM_ERR_BOUNDS);
                                     need &= ~(1u << q);
                                     continue;
                                 }
-                                bits2 |= (cc & 31u) << (5 * q);
-                                d2[q] = ld_trie_u2(t.deep + (cc >> 5), tpol);
+                                bits2 |= (cq & 31u) << (5 * q);
+                                d2[q] = ld_trie_u2(t.deep + (cq >> 5), tpol);
                                 dm |= 1u << q;
                             }
 #pragma unroll
@@ -1121,6 +1138,8 @@ int launch_scan(const TrieDev &t, const pm_config &cfg, const ScanArgs &a, void 
     for (int32_t i = 1; i < cfg.dense_k; ++i) p.ck1 *= t.C;
     p.deep_on = cfg.deep && t.deep_k > 0 && t.C != 256 ? 1u : 0u;
     p.kload = (uint32_t)cfg.dense_k + 4u;
+    p.uk1 = 1u;
+    for (uint32_t i = 1; i < t.deep_k; ++i) p.uk1 *= t.deep_U;
     if (p.deep_on && t.deep_k + 4u > p.kload) p.kload = t.deep_k + 4u;
     p.gram = t.gram[cfg.dense_k];
     p.binary = cfg.row_search ? 1u : 0u;
