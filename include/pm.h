@@ -24,7 +24,7 @@
  *    crosses this boundary.
  *  - Pointers named d_* are CUDA device pointers on the current device;
  *    h_* are host pointers. The caller owns every buffer it passes; libpm
- *    owns only what a pm_trie / pm_server handle holds.
+ *    owns only what a pm_trie, pm_server or pm_scanner handle holds.
  *  - pm_stream is the driver stream type (identical to cudaStream_t); NULL
  *    is the legacy default stream. Scans are asynchronous on that stream.
  *  - Errors raised inside a kernel (a bounded wait that ran out, a bounds

@@ -1,31 +1,45 @@
 // PFAC scan kernels for sm_103a (Section II-C: one failure-less walk per
 // start position over the CRS trie of Section III).
 //
-// One persistent kernel serves the single-text scan and the batched scan.
-// Each CTA owns every gridDim.x-th tile of the (concatenated) text:
+// One persistent, warp-specialized kernel serves the single-text and the
+// batched scan; one 1024-thread CTA per SM. After the CTA loads the shared
+// tables (its only CTA-wide barrier), its warps split in two.
 //
-//  a1 staging   thread 0 streams tile + halo (>= longest pattern) into one of
+// Producer warps, each an independent pipeline over its own text tiles:
+//  a1 staging   lane 0 streams tile + halo (>= longest pattern) into one of
 //               `stages` shared-memory buffers with a 1-D TMA bulk copy
 //               completing on an mbarrier, `stages` tiles ahead (text whose
 //               base is not 16-byte aligned is staged with plain loads);
-//  a2 dense     the first k trie levels are resolved by one lookup of the
-//               k-gram of byte classes in a shared-memory bitmap with rank
-//               words (the depth-k node = first + rank);
-//  a3 CRS walk  deeper levels walk the CRS rows in global memory (read-only
-//               path, L2-resident) until the first mismatch or the text end;
-//               an optional 32-bit child filter of the depth-k node skips
-//               the first row search when the next byte cannot follow;
+//  a2 filter    four consecutive positions per lane: a blocked Bloom probe
+//               of each 4-gram (byte alphabet) or an exact test of each
+//               (k+1)-gram of byte classes, in shared memory; a position
+//               that fails cannot match (every pattern is longer);
+//     start     a passing position's depth-k node from the dense bitmap +
+//               rank table (shared memory); byte-class tries also look up
+//               the deep level's bitmap + rank table in L2, settling most
+//               positions there;
+//  a4 -1        every position gets -1 (one 16-byte streaming store per
+//               lane); walks that match patch their id later;
+//     hand-off  each remaining walk {position, start depth, start node,
+//               text} goes to a shared-memory ring (ballot/popc compaction,
+//               per-cell sequence numbers).
+// Walker warps take up to 32 ring entries at a time, one walk per lane:
+//  a3 CRS walk  each step reads the node's 16-byte row record (row start,
+//               length, has-match bit, first eight column bytes) with the
+//               next text byte; the child of non-zero e is node e + 1 (BFS
+//               order); longer rows are searched in the column array. With
+//               layout 1 the walk reads the bitmapped nodes of Section III
+//               instead (256-bit child bitmap + first child, rank gives the
+//               child);
 //  a4 emit      ids[i] = best[v], count += nfinal[v] of the deepest node v;
-//               four consecutive positions per thread give one 16-byte store;
-//  a5 reduce    per-text counts are summed in registers and flushed with one
-//               atomic per (thread, text) that saw a match, or per CTA for a
-//               single text after a warp/CTA reduction.
+//  a5 reduce    per-lane counts, warp shuffle reduction, one atomic per warp
+//               (per match and text in batch mode).
 //
-// Every wait on an mbarrier is bounded by a clock budget; on expiry the CTA
-// records PM_ERR_TIMEOUT in a device word, waits (bounded) for its copies in
-// flight and returns. The checked variant bounds-checks every shared and
-// global index and records PM_ERR_BOUNDS instead of touching memory out of
-// range.
+// Every wait (mbarriers, ring cells, idle walkers) is bounded by a clock
+// budget counted from the last progress; on expiry the warp records
+// PM_ERR_TIMEOUT in a device word, waits (bounded) for its copies in flight
+// and returns. The checked variant bounds-checks every shared and global
+// index and records PM_ERR_BOUNDS instead of touching memory out of range.
 #include <cuda_runtime.h>
 
 #include <atomic>
@@ -243,10 +257,9 @@ __device__ __forceinline__ uint32_t find_text(const uint64_t *off, uint32_t ntex
 }
 
 // Walk ring, in shared memory, between the producer warps (tiles, filter)
-// and the walker warps (CRS walks). An entry is one 4-position group with at
-// least one position to walk: x = position of the group (low 32 bits), y =
-// its high 24 bits | positions to walk << 24 | of those, positions walked
-// from the root << 28, z, w = the group's text bytes [pos, pos+8).
+// and the walker warps (CRS walks). An entry is one walk (walk_entry_of):
+// x = start position (low 32 bits), y = its bits 32..39 | start depth << 8,
+// z = start node, w = text index (batch) or 0xFFFFFFFF.
 // Each cell carries a sequence number (a bounded multi-producer,
 // multi-consumer ring): cell i starts at i; the producer of slot s waits for
 // s, fills the cell and sets s+1; the walker of slot s waits for s+1, takes
