@@ -139,10 +139,16 @@ class ClockSampler:
 
 
 def kernel_source_sha():
+    """sha256 of the scan kernel's source (pm_scan.cu, pm_internal.h) with
+    comments and blank lines removed: a profile stays valid across
+    comment-only edits and is dropped by any change to the code."""
     h = hashlib.sha256()
     for f in ("pm_scan.cu", "pm_internal.h"):
-        with open(os.path.join(ROOT, "paper_1702_03657_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, "paper_1702_03657_gb300", "csrc", f)) as fh:
+            txt = fh.read()
+        txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+        txt = re.sub(r"//[^\n]*", "", txt)
+        h.update("\n".join(l.rstrip() for l in txt.splitlines() if l.strip()).encode())
     return h.hexdigest()
 
 
