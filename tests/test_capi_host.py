@@ -198,6 +198,32 @@ def test_scanner_host_side(lib):
     assert lib.pm_scanner_close(None) == pm.PM_OK
 
 
+def test_autotune_candidates_host(lib):
+    """The autotuner's candidates are valid configurations (the library
+    accepts each), distinct, span few to most walker warps, keep the deep
+    level on where the trie has one, and leave the handle's configuration
+    as it was."""
+    from paper_1702_03657_gb300 import tune
+    rng = np.random.Generator(np.random.MT19937(4))
+    pats = [rng.choice(list(b"ACGT"), size=int(rng.integers(14, 21))).astype(np.uint8).tobytes()
+            for _ in range(400)]
+    t = pm.pm_build_host(pats)
+    base = pm.pm_get_config(t)
+    cands = tune.candidates(t, 1 << 20)
+    assert len(cands) >= 20
+    assert pm.pm_get_config(t) == base
+    seen = set()
+    for c in cands:
+        pm.pm_set_config(t, c)
+        assert 1 <= c["walkers"] < c["threads"] // 32
+        assert c["deep"] == 1 and c["layout"] == 0
+        seen.add(tuple(sorted(c.items())))
+    assert len(seen) == len(cands)
+    shares = {c["walkers"] / (c["threads"] // 32) for c in cands}
+    assert min(shares) < 0.1 and max(shares) > 0.8
+    pm.pm_set_config(t, base)
+
+
 def test_server_rejects_host_only_trie(lib):
     t = pm.pm_build_host([b"abc", b"abd"])
     with pytest.raises(pm.PMError) as e:
