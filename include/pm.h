@@ -134,7 +134,8 @@ int pm_build_host(const uint8_t *const *patterns, const uint32_t *lengths,
                   uint32_t n, pm_trie **out, uint64_t *footprint_bytes);
 
 /* Frees the handle and its device memory. NULL is ignored. The caller must
- * ensure no scan on it is still running. */
+ * ensure no scan on it is still running, and destroy or close the servers
+ * and scanners made from it first (they keep a pointer to it). */
 void pm_free(pm_trie *h);
 
 /* Sizes of the trie. Errors: PM_ERR_INVAL. */
