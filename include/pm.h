@@ -25,8 +25,9 @@
  *  - Pointers named d_* are CUDA device pointers on the current device;
  *    h_* are host pointers. The caller owns every buffer it passes; libpm
  *    owns only what a pm_trie, pm_server or pm_scanner handle holds.
- *  - pm_stream is the driver stream type (identical to cudaStream_t); NULL
- *    is the legacy default stream. Scans are asynchronous on that stream.
+ *  - pm_stream is the CUDA stream type (CUstream_st *, identical to
+ *    cudaStream_t); NULL is the legacy default stream. Scans are
+ *    asynchronous on that stream.
  *  - Errors raised inside a kernel (a bounded wait that ran out, a bounds
  *    violation in the checked scan) are recorded in a device word and
  *    reported by pm_device_error(); the kernel returns instead of trapping.
@@ -294,8 +295,8 @@ int pm_scan_host(pm_trie *h, const uint8_t *h_text, uint64_t len,
 int pm_scan_host_static(const pm_trie *h, const uint8_t *h_text, uint64_t len,
                         int32_t *h_ids, int64_t *h_count, pm_stream stream);
 
-/* ---- serving: continuous batching (SURVEY north star (b); the paper has a
- * single batch-free scan, Section II-C) ------------------------------------
+/* ---- serving: continuous batching (a service of the library; the paper has
+ * a single batch-free scan, Section II-C) ----------------------------------
  * A server keeps the trie resident and runs a scheduler thread that
  *  - admits submitted requests in arrival order as batch slots and device
  *    memory (a first-fit arena for request texts) free up,
