@@ -224,6 +224,30 @@ def test_autotune_candidates_host(lib):
     pm.pm_set_config(t, base)
 
 
+def test_binding_checks_arguments(lib):
+    """The binding refuses host tensors, wrong dtypes, non-contiguous views
+    and malformed match buffers before calling into the library."""
+    torch = pytest.importorskip("torch")
+    t = pm.pm_build_host([b"abc"])
+    text = torch.zeros(16, dtype=torch.uint8)
+    ids = torch.zeros(16, dtype=torch.int32)
+    cnt = torch.zeros(1, dtype=torch.int64)
+    for call in (lambda: pm.pm_scan(t, text, ids, cnt),
+                 lambda: pm.pm_scan_batch(t, text, torch.zeros(2, dtype=torch.int64), ids, cnt),
+                 lambda: pm.pm_scan_all(t, text, ids, cnt, torch.zeros((4, 2), dtype=torch.int64),
+                                        torch.zeros(1024, dtype=torch.uint8)),
+                 lambda: pm.pm_scan_all(t, text, ids, cnt, torch.zeros(8, dtype=torch.int64),
+                                        torch.zeros(1024, dtype=torch.uint8)),
+                 lambda: pm.pm_scan_walks(t, text, ids, cnt, cnt)):
+        with pytest.raises(pm.PMError) as e:
+            call()
+        assert e.value.code == pm.PM_ERR_INVAL
+    with pytest.raises(pm.PMError):
+        pm._dptr(torch.zeros(4, dtype=torch.float32), torch.int32, "ids")
+    with pytest.raises(pm.PMError):
+        pm._offsets_ptr(torch.zeros(3, dtype=torch.int32))
+
+
 def test_server_rejects_host_only_trie(lib):
     t = pm.pm_build_host([b"abc", b"abd"])
     with pytest.raises(pm.PMError) as e:
