@@ -392,3 +392,29 @@ def test_mutations_are_caught(tmp_path, k):
         for got in _run_mutant(lib, case["patterns"], case["text"]):
             caught |= got != exp
     assert caught, f"mutation {k} not caught"
+
+
+def test_property_definition_equals_walk():
+    """Random small pattern sets and texts (property-based): the definition
+    and the walk agree on ids, count, lookups and the all-matches list, and
+    both equal the plain-Python brute force."""
+    hyp = pytest.importorskip("hypothesis")
+    st = pytest.importorskip("hypothesis.strategies")
+
+    alpha = st.sampled_from([b"ab", b"abc", b"\x00\xff", b"acgt"])
+
+    @hyp.settings(max_examples=150, deadline=None, derandomize=True)
+    @hyp.given(alpha.flatmap(lambda a: st.tuples(
+        st.lists(st.binary(min_size=1, max_size=6).map(
+            lambda b: bytes(a[x % len(a)] for x in b)), min_size=1, max_size=12),
+        st.binary(max_size=80).map(lambda b: bytes(a[x % len(a)] for x in b)))))
+    def check(case):
+        pats, text = case
+        exp_ids, exp_cnt, exp_look = py_brute(pats, text)
+        for ids, cnt, look in both(pats, text):
+            assert ids.tolist() == exp_ids and cnt == exp_cnt and look == exp_look
+        exp_all = py_brute_all(pats, text)
+        for got in both_all(pats, text):
+            assert got == exp_all
+
+    check()
