@@ -276,15 +276,20 @@ int pm_scan_host(pm_trie *h, const uint8_t *h_text, uint64_t len,
  * device-synchronising stalls on the request path. The paper has no
  * counterpart: this is a service of the library, not part of the method.
  * The text (at most PM_STATIC_MAX_LEN bytes), its ids and its count are
- * staged in one statically sized device array inside libpm (about 5 MiB,
- * held on every GPU that loads the library until the process exits). No
- * cudaMalloc, cudaFree or allocating library routine is called. The caller
+ * staged in one statically sized device array inside libpm (about 5 MiB).
+ * CUDA places the array on a GPU when the library's module that holds it is
+ * loaded there: at the first pm_scan_host_static call on that GPU under the
+ * default lazy module loading, at context creation when modules are loaded
+ * eagerly. It stays until the process exits. No cudaMalloc, cudaFree or
+ * allocating library routine is called. The caller
  * passes the host text h_text[0..len) and receives h_ids int32[len] and
  * *h_count; the copies and the scan run on `stream` (NULL: the legacy
  * default stream) and the call returns once the results are on the host.
  * The first call on a device looks up the array's device address for that
- * device (cudaGetSymbolAddress, with that device current); make that first
- * call before any stream capture on the device.
+ * device (cudaGetSymbolAddress, with that device current) and keeps it for
+ * the life of the process; make that first call before any stream capture
+ * on the device. cudaDeviceReset after that first call is not supported:
+ * the kept address would belong to the destroyed context.
  * Every call uses the same array, which keeps the last call's contents;
  * each call overwrites all its ids and zeroes the count first. Calls whose
  * work overlaps on the GPU (other streams, other host threads) race on the

@@ -20,8 +20,10 @@
 namespace {
 
 // Layout of the scratch array: [text: PM_STATIC_MAX_LEN][ids: 4 *
-// PM_STATIC_MAX_LEN][count: 8], each part 256-byte aligned. Every GPU that
-// loads libpm holds this array (about 5 MiB) until the process exits.
+// PM_STATIC_MAX_LEN][count: 8], each part 256-byte aligned. A GPU holds this
+// array (about 5 MiB) from the time this file's module is loaded there (its
+// first use under lazy module loading, context creation under eager
+// loading) until the process exits.
 constexpr uint64_t kTextOff = 0;
 constexpr uint64_t kIdsOff = PM_STATIC_MAX_LEN;
 constexpr uint64_t kCountOff = kIdsOff + 4ull * PM_STATIC_MAX_LEN;
@@ -30,8 +32,10 @@ constexpr uint64_t kScratchBytes = kCountOff + 256;
 static __device__ __align__(256) unsigned char g_pm_static_scratch[kScratchBytes];
 
 // Device address of the scratch array, resolved once per device (with that
-// device current) and cached: the array's name in host code is only a host
-// stand-in for the symbol, not a device address.
+// device current) and cached for the life of the process: the array's name
+// in host code is only a host stand-in for the symbol, not a device address.
+// A cudaDeviceReset would leave the cached address stale; the header states
+// that it is not supported after the first call.
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
 void *g_addr[kMaxDevices] = {};

@@ -392,10 +392,24 @@ def pm_scan_ex(trie: Trie, texts, offsets, ids, counts, lookups=None,
         C.byref(c) if c is not None else None, _stream_ptr(stream)), "pm_scan_ex")
 
 
+def _host_arrays(text: np.ndarray, ids: np.ndarray, where: str):
+    """Checks a host text (uint8) and id buffer (int32): both C-contiguous,
+    ids at least as long as the text (the C ABI reads and writes them as
+    flat arrays)."""
+    if text.dtype != np.uint8 or ids.dtype != np.int32:
+        raise PMError(PM_ERR_INVAL, where, "text must be uint8 and ids int32")
+    if not (text.flags.c_contiguous and ids.flags.c_contiguous):
+        raise PMError(PM_ERR_INVAL, where, "text and ids must be C-contiguous")
+    if not ids.flags.writeable:
+        raise PMError(PM_ERR_INVAL, where, "ids must be writeable")
+    if ids.size < text.size:
+        raise PMError(PM_ERR_INVAL, where, "ids shorter than the text")
+
+
 def pm_scan_host(trie: Trie, text: np.ndarray, ids: np.ndarray) -> int:
     """Scan a host text (uint8 numpy, ideally pinned) into host ids (int32);
     returns the count."""
-    assert text.dtype == np.uint8 and ids.dtype == np.int32 and ids.size >= text.size
+    _host_arrays(text, ids, "pm_scan_host")
     cnt = C.c_int64()
     _check(load().pm_scan_host(trie.handle, text.ctypes.data if text.size else None,
                                text.size, ids.ctypes.data if ids.size else None,
@@ -406,7 +420,7 @@ def pm_scan_host(trie: Trie, text: np.ndarray, ids: np.ndarray) -> int:
 def pm_scan_host_static(trie: Trie, text: np.ndarray, ids: np.ndarray, stream=None) -> int:
     """pm_scan_host without any device allocation (text <= PM_STATIC_MAX_LEN
     bytes, staged in libpm's static device array); returns the count."""
-    assert text.dtype == np.uint8 and ids.dtype == np.int32 and ids.size >= text.size
+    _host_arrays(text, ids, "pm_scan_host_static")
     cnt = C.c_int64()
     _check(load().pm_scan_host_static(trie.handle, text.ctypes.data if text.size else None,
                                       text.size, ids.ctypes.data if ids.size else None,

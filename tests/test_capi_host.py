@@ -246,6 +246,28 @@ def test_binding_checks_arguments(lib):
         pm._dptr(torch.zeros(4, dtype=torch.float32), torch.int32, "ids")
     with pytest.raises(pm.PMError):
         pm._offsets_ptr(torch.zeros(3, dtype=torch.int32))
+    # host-buffer entry points: C-contiguous uint8 text, int32 ids
+    text_h = np.zeros(64, np.uint8)
+    ids_h = np.zeros(64, np.int32)
+    for f in (pm.pm_scan_host, pm.pm_scan_host_static):
+        for a, b in ((text_h[::2], ids_h[:32]), (text_h, ids_h[::2]),
+                     (text_h.astype(np.int8), ids_h), (text_h, ids_h[:10])):
+            with pytest.raises(pm.PMError) as e:
+                f(t, a, b)
+            assert e.value.code == pm.PM_ERR_INVAL
+
+
+def test_header_constants_match_binding(lib):
+    """The binding's copies of pm.h's constants and error codes are the
+    header's."""
+    src = open(B.INCLUDE + "/pm.h").read()
+    defs = {}
+    for name, val in re.findall(r"#define[ \t]+(PM_[A-Z_]+)[ \t]+([^\n/]+)", src):
+        v = val.strip().replace("ull", "").rstrip("u")
+        defs[name] = int(eval(v))
+    for name, val in defs.items():
+        assert getattr(pm, name) == val, name
+    assert "PM_STATIC_MAX_LEN" in defs and "PM_ERR_HOST_ONLY" in defs
 
 
 def test_server_rejects_host_only_trie(lib):

@@ -1,9 +1,10 @@
 """GPU parity: the CUDA scan through the C ABI against the CPU oracle.
 
 Integer work, so the bar is bit-exact: every ids[i] and every count equal
-the oracle's on the same seeded input. Small cases compare every position;
-the full-size workloads (in the launch configuration the benchmark times)
-compare sampled windows position by position plus the total count.
+the oracle's on the same seeded input. Every test compares every position,
+the full-size workloads included (in the launch configuration the benchmark
+times). A text longer than 2^32 bytes checks the start positions past 32
+bits (test_gpu_large.py).
 """
 import os
 
@@ -429,30 +430,28 @@ def check_windows(ot, text, ids, windows):
 
 
 def test_paper_scale_full_size():
+    """Every one of the 268 M positions and the count, in the benchmark's
+    launch configuration; sampled windows first for a quick failure report."""
     wl = W.paper_scale(0)
     t = pm.pm_build(wl.patterns)
     ids, cnt, _ = gpu_scan(t, wl.text)
     ot = oracle.Trie(wl.patterns)
     check_windows(ot, wl.text, ids, sampled_windows(len(wl.text), 48, 4096, 1))
-    # positions with a match must hold the oracle's longest id
-    hits = np.flatnonzero(ids >= 0)
-    assert hits.size >= 4096
-    sel = hits[:: max(1, hits.size // 2000)]
-    for i in sel[:2000]:
-        o, _, _ = ot.scan(wl.text, int(i), int(i) + 1)
-        assert o[0] == ids[i]
-    _, o_cnt, _ = ot.scan(wl.text, threads=HOST_THREADS)
-    assert cnt == o_cnt
+    assert int((ids >= 0).sum()) >= 4096
+    o_ids, o_cnt, _ = ot.scan(wl.text, threads=HOST_THREADS)
+    assert_same(ids, cnt, o_ids, o_cnt)
 
 
 def test_acgt_full_size():
+    """Every one of the 1,074 M positions and the count (1 GiB ACGT text)."""
     wl = W.acgt(0)
     t = pm.pm_build(wl.patterns)
     ids, cnt, _ = gpu_scan(t, wl.text)
     ot = oracle.Trie(wl.patterns)
     check_windows(ot, wl.text, ids, sampled_windows(len(wl.text), 32, 4096, 2))
-    _, o_cnt, _ = ot.scan(wl.text, threads=HOST_THREADS)
-    assert cnt == o_cnt
+    o_ids, o_cnt, _ = ot.scan(wl.text, threads=HOST_THREADS)
+    assert_same(ids, cnt, o_ids, o_cnt)
+    del o_ids
 
 
 def test_autotune_keeps_bits():
