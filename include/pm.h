@@ -91,28 +91,36 @@ typedef struct {
                              /* byte-class tries only, 0 if none               */
 } pm_trie_stats;
 
-/* Launch configuration of the scan kernel (picked by an autotuner). The
- * producer warps of a CTA are independent pipelines over their own text
- * tiles; they queue the positions that need a trie walk in a shared ring
- * that the walker warps drain. */
+/* Launch configuration of the scan kernel (picked by an autotuner). Every
+ * warp of a CTA is an independent pipeline over its own text tiles: it
+ * stages them, tests each start position in the shared-memory filter, and
+ * walks the positions that remain in rounds of 32 (one per lane) from its
+ * own queue. */
 typedef struct {
-    int32_t threads;      /* threads per CTA: 128, 256, 512 or 1024           */
-    int32_t tile;         /* text bytes per warp tile: multiple of 128,       */
-                          /* 128 .. 32768                                     */
-    int32_t dense_k;      /* trie levels resolved in shared memory before a   */
-                          /* CRS walk: 0 .. dense_k_max (< shortest pattern)  */
-    int32_t filter_bits;  /* child-filter width per k-gram: 8, 16 or 32       */
+    int32_t threads;      /* threads per CTA: a multiple of 32, 128 .. 1024   */
+    int32_t tile;         /* text bytes per warp tile: a multiple of          */
+                          /* 32 * positions, 256 .. 32768                     */
+    int32_t dense_k;      /* byte alphabet: trie levels resolved before a     */
+                          /* walk, 0 .. dense_k_max (< shortest pattern);     */
+                          /* byte classes: depth F of the filter's grams,     */
+                          /* 0 (none) .. dense_k_max (<= shortest pattern)    */
+    int32_t filter_bits;  /* byte alphabet: filter width per k-gram, 8, 16 or */
+                          /* 32; byte classes: 8                              */
     int32_t row_search;   /* 0: linear, 1: binary search of the byte column   */
     int32_t ctas_per_sm;  /* persistent grid = SMs * ctas_per_sm (0: maximum) */
-    int32_t stages;       /* tiles in flight per producer warp (TMA), 2..4    */
+    int32_t stages;       /* tiles in flight per warp (TMA), 2..4             */
     int32_t checked;      /* 1: bounds-checked scan (PM_ERR_BOUNDS on error)  */
-    int32_t walkers;      /* warps per CTA that run the CRS walks the others  */
-                          /* queue, 1 .. threads/32 - 1                       */
-    int32_t deep;         /* 1: positions passing the filter look up the deep */
-                          /* level before walking (needs deep_k > 0), 0: not */
+    int32_t positions;    /* start positions per lane and group: 4 or 8       */
+    int32_t deep;         /* byte classes: 1: positions passing the filter    */
+                          /* look up the deep level before walking, 0: they  */
+                          /* walk from the root; byte alphabet: 0             */
     int32_t layout;       /* trie form the walks read: 0 CRS row records (16  */
                           /* bytes a node), 1 the bitmapped node of Section  */
                           /* III (256-bit child bitmap + first child, 36 B)  */
+    int32_t wait_clocks;  /* bound of each wait for a staged tile, in SM      */
+                          /* clocks; 0: the default, about 2 s. A wait that  */
+                          /* runs out records PM_ERR_TIMEOUT (pm_device_error) */
+                          /* and ends the scan early                          */
 } pm_config;
 
 /* ---- trie construction (Section III, steps I, II, VI and the CRS step) --

@@ -70,13 +70,26 @@ int32_t pick_bits(const pm_trie *h, int32_t k)
     return 0;
 }
 
-// Default launch configuration: one 1024-thread CTA per SM, 1-2 KiB
-// producer tiles double-buffered, the deepest filter level that fits; for
-// the byte alphabet's Bloom filter the wider filter with smaller tiles comes
-// first (fewer walks). The walker warps' share follows the expected share
-// of positions that need a walk: 3/16 of the warps behind the deep level
-// (with 1 KiB tiles), most of them when an exact filter passes most
-// positions, an eighth otherwise. An autotuner may refine it.
+// Thread counts tried for a CTA, largest first (one CTA per SM).
+const int32_t kThreadChoices[] = {1024, 992, 960, 928, 896, 768, 512, 384, 256, 128};
+
+// Byte classes: whether a lane's window of packed classes (its chunk of
+// `positions` classes and the neighbour chunks covering the deepest gram it
+// reads) fits the kernel's 64-bit window.
+bool window_fits(const pm_trie *h, const pm_config &c)
+{
+    if (h->host.C == 256) return true;
+    const pm::ScanLayout L = pm::scan_layout(h->dev, c);
+    const uint32_t pcb = (uint32_t)c.positions * h->host.cb;
+    return pcb <= 32 && (1 + L.nnb) * pcb <= 64 && L.nnb <= 8;
+}
+
+// Default launch configuration: one CTA per SM, 1 KiB tiles double-buffered
+// with as many warps as the shared memory allows, eight positions per lane
+// where the window allows, and the deepest filter level that fits. For
+// the byte alphabet's Bloom filter the wider filter comes first (fewer
+// walks); byte-class tries look up the deep level behind their filter. An
+// autotuner may refine it.
 pm_config default_config(const pm_trie *h, int smem_limit)
 {
     pm_config c{};
@@ -84,48 +97,32 @@ pm_config default_config(const pm_trie *h, int smem_limit)
     c.ctas_per_sm = 0;
     c.stages = 2;
     c.checked = 0;
-    c.deep = h->host.deep_k > 0 ? 1 : 0;
     c.layout = 0;
+    c.wait_clocks = 0;
+    const bool ident = h->host.C == 256;
+    c.deep = !ident && h->host.deep_k > 0 ? 1 : 0;
     const uint64_t limit = (uint64_t)smem_limit - 1024;
     struct Pref {
         int32_t bits, tile;
     };
     for (int32_t k = (int32_t)h->host.dense_k_max; k >= 0; --k) {
         c.dense_k = k;
-        const bool bloom = h->host.C == 256 && k >= 2;
-        // Share of positions that pass an exact filter: the (k+1)-grams over
-        // the used classes that are root paths. Walkers get a share of the
-        // warps to match (the Bloom filter passes well under 1 %).
-        double pass = 0.0;
-        if (!bloom) {
-            double space = 1.0;
-            const double used = h->host.C == 256 ? 256.0 : (double)h->host.C - 1.0;
-            for (int32_t j = 0; j <= k; ++j) space *= std::max(used, 1.0);
-            const std::vector<uint32_t> &lv = h->host.level_nodes;
-            const double paths = (size_t)k + 1 < lv.size() ? lv[k + 1] : 0.0;
-            pass = std::min(1.0, paths / space);
-        }
         std::vector<Pref> prefs;
-        if (bloom) prefs = {{16, 1024}, {8, 2048}, {8, 1536}, {8, 1024}};
-        const int32_t exact = pick_bits(h, k);
-        if (c.deep) {
-            for (int32_t tile : {1024, 2048, 512, 256, 128}) prefs.push_back({exact, tile});
-        } else {
-            for (int32_t tile : {2048, 1536, 1024, 512, 256, 128}) prefs.push_back({exact, tile});
-        }
-        for (int32_t threads : {1024, 512, 256, 128}) {
-            for (const Pref &pf : prefs) {
-                if (!have_filter(h, k, pf.bits)) continue;
-                c.threads = threads;
-                c.tile = pf.tile;
-                c.filter_bits = pf.bits;
-                const int32_t warps = threads / 32;
-                c.walkers = c.deep          ? warps * 3 / 16
-                            : pass > 0.3    ? warps * 7 / 8
-                            : pass > 0.05   ? warps / 2
-                                            : warps / 8;
-                c.walkers = std::min(std::max<int32_t>(1, c.walkers), warps - 1);
-                if (pm::scan_smem_bytes(h->dev, c) <= limit) return c;
+        if (ident && k >= 2) prefs = {{16, 1024}, {8, 2048}, {8, 1024}};
+        const int32_t exact = ident ? pick_bits(h, k) : 8;
+        for (int32_t tile : {1024, 2048, 512, 256}) prefs.push_back({exact, tile});
+        for (const Pref &pf : prefs) {
+            for (int32_t threads : kThreadChoices) {
+                for (int32_t pos : {8, 4}) {
+                    if (ident ? !have_filter(h, k, pf.bits) : pf.bits != 8) continue;
+                    if (pf.tile % (32 * pos) != 0) continue;
+                    c.threads = threads;
+                    c.tile = pf.tile;
+                    c.filter_bits = pf.bits;
+                    c.positions = pos;
+                    if (!window_fits(h, c)) continue;
+                    if (pm::scan_smem_bytes(h->dev, c) <= limit) return c;
+                }
             }
         }
     }
@@ -133,26 +130,32 @@ pm_config default_config(const pm_trie *h, int smem_limit)
     c.filter_bits = 8;
     c.threads = 128;
     c.tile = 128;
-    c.walkers = 1;
+    c.positions = 4;
     return c;
 }
 
 int validate_config(const pm_trie *h, const pm_config &c, std::string &why)
 {
-    if (c.threads != 128 && c.threads != 256 && c.threads != 512 && c.threads != 1024) {
-        why = "threads must be 128, 256, 512 or 1024";
+    const bool ident = h->host.C == 256;
+    if (c.threads < 128 || c.threads > 1024 || c.threads % 32 != 0) {
+        why = "threads must be a multiple of 32 in [128, 1024]";
         return PM_ERR_INVAL;
     }
-    if (c.tile < 128 || c.tile > 32768 || c.tile % 128 != 0) {
-        why = "tile must be a multiple of 128 in [128, 32768]";
+    if (c.positions != 4 && c.positions != 8) {
+        why = "positions must be 4 or 8";
+        return PM_ERR_INVAL;
+    }
+    if (c.tile < 32 * c.positions || c.tile > 32768 || c.tile % (32 * c.positions) != 0) {
+        why = "tile must be a multiple of 32 * positions in [32 * positions, 32768]";
         return PM_ERR_INVAL;
     }
     if (c.dense_k < 0 || (uint32_t)c.dense_k > h->host.dense_k_max) {
         why = "dense_k must be in 0..dense_k_max";
         return PM_ERR_INVAL;
     }
-    if (!have_filter(h, c.dense_k, c.filter_bits)) {
-        why = "no filter of this width at this dense_k (widths 8, 16, 32)";
+    if (ident ? !have_filter(h, c.dense_k, c.filter_bits) : c.filter_bits != 8) {
+        why = ident ? "no filter of this width at this dense_k (widths 8, 16, 32)"
+                    : "byte-class tries take filter_bits 8";
         return PM_ERR_INVAL;
     }
     if (c.stages < 2 || c.stages > 4) {
@@ -163,10 +166,6 @@ int validate_config(const pm_trie *h, const pm_config &c, std::string &why)
         why = "ctas_per_sm must be 0..32";
         return PM_ERR_INVAL;
     }
-    if (c.walkers < 1 || c.walkers >= c.threads / 32) {
-        why = "walkers must be in 1 .. threads/32 - 1";
-        return PM_ERR_INVAL;
-    }
     if (c.row_search < 0 || c.row_search > 1 || c.checked < 0 || c.checked > 1) {
         why = "row_search and checked are 0 or 1";
         return PM_ERR_INVAL;
@@ -175,8 +174,16 @@ int validate_config(const pm_trie *h, const pm_config &c, std::string &why)
         why = "layout is 0 (CRS row records) or 1 (bitmapped nodes)";
         return PM_ERR_INVAL;
     }
-    if (c.deep < 0 || c.deep > 1 || (c.deep == 1 && h->host.deep_k == 0)) {
-        why = "deep is 0, or 1 when the trie has a deep level";
+    if (c.deep < 0 || c.deep > 1 || (c.deep == 1 && (ident || h->host.deep_k == 0))) {
+        why = "deep is 0, or 1 when the trie has a deep level (byte classes)";
+        return PM_ERR_INVAL;
+    }
+    if (c.wait_clocks < 0) {
+        why = "wait_clocks must be >= 0";
+        return PM_ERR_INVAL;
+    }
+    if (!window_fits(h, c)) {
+        why = "positions x bits per class too wide for the window at this filter and deep level";
         return PM_ERR_INVAL;
     }
     uint64_t need = pm::scan_smem_bytes(h->dev, c);
@@ -198,8 +205,9 @@ void fill_dev_sizes(pm_trie *h)
     d.min_len = t.n_patterns ? t.min_len : 0xFFFFFFFFu;
     d.max_len = t.max_len;
     d.dense_k_max = t.dense_k_max;
+    d.cb = t.cb;
+    d.other_check = t.other_check;
     d.deep_k = t.deep_k;
-    d.deep_U = t.deep_U;
     d.deep_first = t.deep_first;
     d.deep_words = (uint32_t)(t.deep.size() / 2);
     d.n_ids = (uint32_t)t.chain.size();
@@ -245,7 +253,7 @@ int upload(pm_trie *h)
     size_t i_row = add(row.data(), 16 * n);
     size_t i_col = add(t.col.data(), nnz);
     size_t i_emit = add(emit.data(), 8 * n);
-    size_t i_cls = add(t.cls, 256);
+    size_t i_cls = add(t.lut, 256);  // byte classes: packed class | "other" flag per byte
     const size_t i_deep = t.deep.empty() ? (size_t)-1 : add(t.deep.data(), 4 * t.deep.size());
     std::vector<int4> minfo(t.chain.size());
     for (size_t i = 0; i < minfo.size(); ++i) minfo[i] = make_int4(t.chain[i], t.plen[i], t.mcnt[i], 0);

@@ -57,6 +57,161 @@ uint64_t ipow_capped(uint64_t C, int k, uint64_t cap)
 
 }  // namespace
 
+// Byte alphabet: the shared-memory filters and dense tables of levels
+// k = 0 .. K, K < shortest pattern, so that no pattern ends within the
+// levels a table resolves (at most two levels: 256^k codes fit the budget).
+int build_byte_tables(HostTrie &t, uint32_t nn, const std::vector<uint32_t> &lvl_begin,
+                      const std::vector<uint32_t> &lvl_count, std::string &msg)
+{
+    const uint32_t m = (uint32_t)t.n_patterns;
+    const uint32_t kcap = m ? std::min<uint32_t>(t.min_len - 1, kMaxDenseK) : 0;
+    uint32_t K = 0;
+    for (uint32_t k = 1; k <= kcap; ++k) {
+        if (ipow_capped(256, (int)k, kFilterBudget) == 0) break;
+        K = k;
+    }
+    t.dense_k_max = K;
+    // code: the path's bytes, first byte most significant (the order in which
+    // BFS numbers each level); fcode: the same path read little-endian (first
+    // byte least significant), as the kernel reads it straight from the text
+    const uint32_t D = K + 2;  // deepest path a filter is built from (Bloom)
+    std::vector<uint64_t> code(nn, 0), fcode(nn, 0);
+    for (uint32_t v = 0; v < nn; ++v) {
+        if (t.depth[v] >= D) break;  // BFS: depths never decrease
+        for (uint32_t e = t.row_ptr[v]; e < t.row_ptr[v + 1]; ++e) {
+            code[t.next[e]] = code[v] * 256 + t.col[e];
+            fcode[t.next[e]] = fcode[v] | ((uint64_t)t.col[e] << (8 * t.depth[v]));
+        }
+    }
+    auto begin = [&](uint32_t d) { return d < lvl_begin.size() ? lvl_begin[d] : nn; };
+    auto count = [&](uint32_t d) { return d < lvl_count.size() ? lvl_count[d] : 0u; };
+    for (uint32_t k = 0; k <= K; ++k) {
+        const uint64_t codes = ipow_capped(256, (int)k, ~0ull);
+        t.first[k] = count(k) ? begin(k) : 0;
+        t.nlevel[k] = count(k);
+        // a Bloom level may test k+2 bytes only if no pattern ends at k+1
+        t.gram[k] = (k >= kBloomK && k + 2 <= 4 && t.min_len >= k + 2) ? k + 2 : k + 1;
+        if (k >= 1) {
+            uint64_t words = (codes + 31) / 32;
+            words += words & 1;  // even: 16-byte units
+            std::vector<uint32_t> &tab = t.dense[k];
+            tab.assign(2 * words, 0);
+            uint64_t prev = 0;
+            for (uint32_t i = 0; i < count(k); ++i) {
+                const uint64_t c = code[begin(k) + i];
+                if (i > 0 && c <= prev) {
+                    msg = "internal: depth-k nodes not in code order";
+                    return PM_ERR_INVAL;
+                }
+                prev = c;
+                tab[2 * (c >> 5)] |= 1u << (c & 31);
+            }
+            uint32_t run = 0;
+            for (uint64_t w = 0; w < words; ++w) {
+                tab[2 * w + 1] = run;
+                run += (uint32_t)__builtin_popcount(tab[2 * w]);
+            }
+        }
+        for (int wi = 0; wi < kFilterWidths; ++wi) {
+            const uint32_t W = 8u << wi;
+            const uint64_t bits = codes * W;
+            if (bits / 8 > kFilterBudget) continue;
+            uint64_t words = (bits + 31) / 32;
+            words = (words + 3) & ~3ull;  // 16-byte units
+            std::vector<uint32_t> &f = t.filter[k][wi];
+            f.assign(words, 0);
+            if (k >= kBloomK) {
+                // blocked Bloom filter of the root paths of length g (read
+                // little-endian) over 2^(8k + log2 W) bits
+                const uint32_t g = t.gram[k];
+                const uint32_t word_bits = 8 * k + (3 + wi) - 5;
+                for (uint32_t i = 0; i < count(g); ++i) {
+                    const BloomProbe b = bloom_probe((uint32_t)fcode[begin(g) + i], g, word_bits);
+                    f[b.word] |= b.mask;
+                }
+                continue;
+            }
+            for (uint32_t i = 0; i < count(k); ++i) {
+                const uint32_t v = begin(k) + i;
+                for (uint32_t e = t.row_ptr[v]; e < t.row_ptr[v + 1]; ++e) {
+                    const uint64_t h = t.col[e] % W;
+                    const uint64_t bit = (h << (8 * k)) | fcode[v];
+                    f[bit >> 5] |= 1u << (bit & 31);
+                }
+            }
+        }
+    }
+    return PM_OK;
+}
+
+// Byte classes: the packed filters of depths F = 1 .. F_max and the deep
+// level of depth D (see pm_internal.h). Both depths are at most the shortest
+// pattern; F_max * cb <= 20 bits (a 128 KiB filter), D * cb <= 26 bits.
+int build_class_tables(HostTrie &t, uint32_t nn, const std::vector<uint32_t> &lvl_begin,
+                       const std::vector<uint32_t> &lvl_count, std::string &msg)
+{
+    const uint32_t m = (uint32_t)t.n_patterns;
+    const uint32_t U = t.C - 1;  // used classes (the last class is "other")
+    uint32_t cb = 1;
+    while ((1u << cb) < U) ++cb;
+    t.cb = cb;
+    t.other_check = U == (1u << cb) ? 1u : 0u;
+    for (int b = 0; b < 256; ++b) {
+        const uint32_t c = t.cls[b];
+        t.lut[b] = c < U ? (uint8_t)c : (uint8_t)(0x80u | (t.other_check ? 0u : U));
+    }
+    const uint32_t FM = m ? std::min<uint32_t>({t.min_len, kFilterCodeBits / cb, (uint32_t)kMaxDenseK}) : 0;
+    const uint32_t D = m ? std::min<uint32_t>(t.min_len, kDeepCodeBits / cb) : 0;
+    t.dense_k_max = FM;
+    // packed path codes of the nodes down to depth D
+    std::vector<uint32_t> pc(nn, 0);
+    for (uint32_t v = 0; v < nn; ++v) {
+        if (t.depth[v] >= D) break;
+        for (uint32_t e = t.row_ptr[v]; e < t.row_ptr[v + 1]; ++e)
+            pc[t.next[e]] = (pc[v] << cb) | t.cls[t.col[e]];
+    }
+    auto begin = [&](uint32_t d) { return d < lvl_begin.size() ? lvl_begin[d] : nn; };
+    auto count = [&](uint32_t d) { return d < lvl_count.size() ? lvl_count[d] : 0u; };
+    for (uint32_t F = 1; F <= FM; ++F) {
+        const uint64_t bits = 1ull << (cb * F);
+        uint64_t words = (bits + 31) / 32;
+        words = (words + 3) & ~3ull;  // 16-byte units
+        std::vector<uint32_t> &f = t.filter[F][0];
+        f.assign(words, 0);
+        for (uint32_t i = 0; i < count(F); ++i) {
+            const uint32_t c = pc[begin(F) + i];
+            f[c >> 5] |= 1u << (c & 31);
+        }
+        t.gram[F] = F;
+        t.first[F] = count(F) ? begin(F) : 0;
+        t.nlevel[F] = count(F);
+    }
+    if (D) {
+        const uint64_t codes = 1ull << (cb * D);
+        uint64_t words = (codes + 31) / 32;
+        words += words & 1;
+        t.deep.assign(2 * words, 0);
+        uint64_t prev = 0;
+        for (uint32_t i = 0; i < count(D); ++i) {
+            const uint64_t c = pc[begin(D) + i];
+            if (i > 0 && c <= prev) {
+                msg = "internal: deep level not in code order";
+                return PM_ERR_INVAL;
+            }
+            prev = c;
+            t.deep[2 * (c >> 5)] |= 1u << (c & 31);
+        }
+        uint32_t run = 0;
+        for (uint64_t w = 0; w < words; ++w) {
+            t.deep[2 * w + 1] = run;
+            run += (uint32_t)__builtin_popcount(t.deep[2 * w]);
+        }
+        t.deep_k = D;
+        t.deep_first = count(D) ? begin(D) : 0;
+    }
+    return PM_OK;
+}
+
 int build_host_trie(const uint8_t *const *patterns, const uint32_t *lengths,
                     uint32_t n, HostTrie &t, std::string &msg)
 {
@@ -185,150 +340,20 @@ int build_host_trie(const uint8_t *const *patterns, const uint32_t *lengths,
     t.level_nodes.assign(t.max_len + 1, 0);
     for (uint32_t v = 0; v < nn; ++v) ++t.level_nodes[t.depth[v]];
 
-    // Top-level tables for k = 0 .. K, K < shortest pattern, so that no
-    // pattern ends within the levels a table resolves.
     for (int k = 0; k <= kMaxDenseK; ++k) {
         t.dense[k].clear();
         for (int w = 0; w < kFilterWidths; ++w) t.filter[k][w].clear();
-        t.first[k] = t.nlevel[k] = 0;
+        t.first[k] = t.nlevel[k] = t.gram[k] = 0;
     }
-    const uint32_t kcap = m ? std::min<uint32_t>(t.min_len - 1, kMaxDenseK) : 0;
-    const uint64_t max_codes = kFilterBudget;  // C^k * 8 bits <= budget
-    uint32_t K = 0;
-    for (uint32_t k = 1; k <= kcap; ++k) {
-        if (ipow_capped(t.C, (int)k, max_codes) == 0) break;
-        K = k;
-    }
-    t.dense_k_max = K;
-
-    // code: base-C code of a node's path (first byte most significant), the
-    // order in which BFS numbers each level. With the byte alphabet the
-    // filter is indexed instead by the little-endian path (first byte least
-    // significant), which the kernel reads straight from the text.
-    const bool le = t.C == 256;
-    // depth of the paths the filters are built from: up to K+2 (Bloom)
-    const uint32_t D = le ? K + 2 : K + 1;
-    std::vector<uint64_t> code(nn, 0), fcode(nn, 0);
-    for (uint32_t v = 0; v < nn; ++v) {
-        if (t.depth[v] >= D) break;  // BFS: depths never decrease
-        for (uint32_t e = t.row_ptr[v]; e < t.row_ptr[v + 1]; ++e) {
-            code[t.next[e]] = code[v] * t.C + t.cls[t.col[e]];
-            fcode[t.next[e]] = le ? fcode[v] | ((uint64_t)t.col[e] << (8 * t.depth[v]))
-                                  : code[t.next[e]];
-        }
-    }
-    std::vector<uint32_t> lvl_begin(K + 3, nn), lvl_count(K + 3, 0);
-    for (uint32_t v = 0; v < nn; ++v) {
-        uint32_t d = t.depth[v];
-        if (d > K + 2) break;
-        if (lvl_count[d]++ == 0) lvl_begin[d] = v;
-    }
-    for (uint32_t k = 0; k <= K; ++k) {
-        const uint64_t codes = ipow_capped(t.C, (int)k, ~0ull);
-        t.first[k] = lvl_count[k] ? lvl_begin[k] : 0;
-        t.nlevel[k] = lvl_count[k];
-        // a Bloom level may test k+2 bytes only if no pattern ends at k+1
-        t.gram[k] = (le && k >= kBloomK && k + 2 <= 4 && t.min_len >= k + 2) ? k + 2 : k + 1;
-        if (k >= 1) {
-            uint64_t words = (codes + 31) / 32;
-            words += words & 1;  // even: copied in 16-byte units
-            std::vector<uint32_t> &tab = t.dense[k];
-            tab.assign(2 * words, 0);
-            uint64_t prev = 0;
-            for (uint32_t i = 0; i < lvl_count[k]; ++i) {
-                const uint64_t c = code[lvl_begin[k] + i];
-                if (i > 0 && c <= prev) {
-                    msg = "internal: depth-k nodes not in code order";
-                    return PM_ERR_INVAL;
-                }
-                prev = c;
-                tab[2 * (c >> 5)] |= 1u << (c & 31);
-            }
-            uint32_t run = 0;
-            for (uint64_t w = 0; w < words; ++w) {
-                tab[2 * w + 1] = run;
-                run += (uint32_t)__builtin_popcount(tab[2 * w]);
-            }
-        }
-        for (int wi = 0; wi < kFilterWidths; ++wi) {
-            const uint32_t W = 8u << wi;
-            const uint64_t bits = codes * W;
-            if (bits / 8 > kFilterBudget) continue;
-            uint64_t words = (bits + 31) / 32;
-            words = (words + 3) & ~3ull;  // 16-byte units
-            std::vector<uint32_t> &f = t.filter[k][wi];
-            f.assign(words, 0);
-            if (le && k >= kBloomK) {
-                // byte alphabet, k >= 2: blocked Bloom filter of the root
-                // paths of length g (read little-endian) over 2^(8k + log2 W)
-                // bits; g = k+2 when no pattern ends at depth k+1
-                const uint32_t g = t.gram[k];
-                const uint32_t word_bits = 8 * k + (3 + wi) - 5;
-                for (uint32_t i = 0; i < lvl_count[g]; ++i) {
-                    const BloomProbe b = bloom_probe((uint32_t)fcode[lvl_begin[g] + i], g, word_bits);
-                    f[b.word] |= b.mask;
-                }
-                continue;
-            }
-            for (uint32_t i = 0; i < lvl_count[k]; ++i) {
-                const uint32_t v = lvl_begin[k] + i;
-                const uint64_t c = fcode[v];
-                for (uint32_t e = t.row_ptr[v]; e < t.row_ptr[v + 1]; ++e) {
-                    const uint64_t h = t.cls[t.col[e]] % W;
-                    // byte alphabet: bit (h << 8k) | path; else: path * W + h
-                    const uint64_t bit = le ? (h << (8 * k)) | c : c * W + h;
-                    f[bit >> 5] |= 1u << (bit & 31);
-                }
-            }
-        }
-    }
-
-    // Deep level (byte classes): the root paths of depth D2, K + 2 <= D2 <
-    // shortest pattern, as a bitmap with ranks over base-U codes, U = the
-    // used classes (a byte of the "other" class is on no path). A position
-    // whose D2-gram is not a root path cannot match (D2 < shortest
-    // pattern); one that is starts its walk at depth D2.
-    t.deep_k = t.deep_U = t.deep_first = 0;
+    t.deep_k = t.deep_first = 0;
     t.deep.clear();
-    if (!le && m > 0) {
-        const uint32_t U = t.C - 1;
-        uint32_t D2 = 0;
-        for (uint32_t d = K + 2; d <= std::min<uint32_t>(t.min_len - 1, kDeepMaxK); ++d) {
-            if (ipow_capped(U, (int)d, kDeepCodes) == 0) break;
-            D2 = d;
-        }
-        if (D2) {
-            std::vector<uint64_t> code2(nn, 0);
-            uint32_t first2 = 0;
-            for (uint32_t d = 0; d < D2; ++d) first2 += t.level_nodes[d];
-            for (uint32_t v = 0; v < first2; ++v)  // BFS: nodes above depth D2
-                for (uint32_t e = t.row_ptr[v]; e < t.row_ptr[v + 1]; ++e)
-                    code2[t.next[e]] = code2[v] * U + t.cls[t.col[e]];
-            const uint64_t codes = ipow_capped(U, (int)D2, ~0ull);
-            uint64_t words = (codes + 31) / 32;
-            words += words & 1;
-            t.deep.assign(2 * words, 0);
-            uint64_t prev = 0;
-            for (uint32_t i = 0; i < t.level_nodes[D2]; ++i) {
-                const uint64_t c = code2[first2 + i];
-                if (t.depth[first2 + i] != D2 || (i > 0 && c <= prev)) {
-                    msg = "internal: deep level not in code order";
-                    return PM_ERR_INVAL;
-                }
-                prev = c;
-                t.deep[2 * (c >> 5)] |= 1u << (c & 31);
-            }
-            uint32_t run = 0;
-            for (uint64_t w = 0; w < words; ++w) {
-                t.deep[2 * w + 1] = run;
-                run += (uint32_t)__builtin_popcount(t.deep[2 * w]);
-            }
-            t.deep_k = D2;
-            t.deep_U = U;
-            t.deep_first = first2;
-        }
-    }
-    return PM_OK;
+    t.cb = t.other_check = 0;
+    std::memset(t.lut, 0, sizeof(t.lut));
+    std::vector<uint32_t> lvl_begin(t.max_len + 2, nn), lvl_count(t.max_len + 2, 0);
+    for (uint32_t v = 0; v < nn; ++v)
+        if (lvl_count[t.depth[v]]++ == 0) lvl_begin[t.depth[v]] = v;
+    return t.C == 256 ? build_byte_tables(t, nn, lvl_begin, lvl_count, msg)
+                      : build_class_tables(t, nn, lvl_begin, lvl_count, msg);
 }
 
 }  // namespace pm

@@ -13,17 +13,15 @@
 
 namespace pm {
 
-// Deepest dense prefix level (trie levels resolved by one table lookup).
-constexpr int kMaxDenseK = 12;
-// Budget of one dense (bitmap + rank) table; it is read from global memory.
-constexpr uint64_t kDenseBudget = 1u << 20;
+// Deepest filter level: the byte alphabet's levels k (k <= 2), or the
+// filter depth F of a byte-class trie (F * bits per class <= 20).
+constexpr int kMaxDenseK = 20;
 // Shared-memory budget of one filter table.
 constexpr uint64_t kFilterBudget = 128u * 1024u;
-// Deep level (byte classes only): the root paths of one depth between the
-// shared-memory levels and the shortest pattern, as a bitmap with ranks read
-// from L2; at most 2^26 codes (16 MiB) and depth 13 (the producer's window).
-constexpr uint64_t kDeepCodes = 1ull << 26;
-constexpr uint32_t kDeepMaxK = 13;
+// Byte classes: bits of a packed filter code (2^20 bits = 128 KiB) and of a
+// deep-level code (2^26 codes, a 16 MiB bitmap with ranks read from L2).
+constexpr uint32_t kFilterCodeBits = 20;
+constexpr uint32_t kDeepCodeBits = 26;
 // All-matches: positions per tile of the match-count table.
 constexpr uint32_t kMatchTileShift = 10;
 // Filter widths: W = 8, 16, 32 bits per k-gram (index 0, 1, 2).
@@ -42,24 +40,38 @@ constexpr int kFilterWidths = 3;
 //
 // Byte classes: the bytes used by some pattern, in ascending byte order, then
 // one class for every other byte (none when all 256 are used: class = byte).
-// A k-gram of classes c_0..c_{k-1} has code sum_j c_j * C^(k-1-j).
 //
-// Dense table of level k (global memory): bit `code` is set iff the k-gram
+// Byte alphabet (C = 256). Dense table of level k (global memory): bit
+// `code` (the k-gram, first byte most significant) is set iff the k-gram
 // spells a root path, and then the depth-k node it reaches is
 //   first[k] + base(word) + popc(word & lower bits),
 // because BFS numbers the depth-k nodes contiguously in code order. Stored
 // as uint2 {bits, base} per 32 codes.
 //
-// Byte alphabet with k >= kBloomK: the filter is instead a blocked Bloom
-// filter over 2^(8k + log2 W) bits of the root paths of length g (g = k+2
-// when every pattern is longer than k+1, else k+1), each read as the
-// little-endian integer x = sum_j b_j << 8j. One multiplicative hash
-// h = hi32((x << (32 - 8g)) * M) picks a 32-bit word (its top bits) and
-// two bits in it (h mod 32 and (h >> 5) mod 32); both are set for every such path. A
-// clear bit proves that the g-gram is not a root path, so the walk stops at
-// depth <= g-1 < shortest pattern. The depth-k node of a passing position is
-// then looked up in the dense table, which also tells whether the k-gram
-// itself is a path.
+// With k >= kBloomK the shared-memory filter is a blocked Bloom filter over
+// 2^(8k + log2 W) bits of the root paths of length g (g = k+2 when every
+// pattern is longer than k+1, else k+1), each read as the little-endian
+// integer x = sum_j b_j << 8j. One multiplicative hash
+// h = hi32((x << (32 - 8g)) * M) picks a 32-bit word (its top bits) and two
+// bits in it (h mod 32 and (h >> 5) mod 32); both are set for every such
+// path. A clear bit proves that the g-gram is not a root path, so the walk
+// stops at depth <= g-1 < shortest pattern. The depth-k node of a passing
+// position is then looked up in the dense table, which also tells whether
+// the k-gram itself is a path.
+//
+// Byte-class tries (C < 256). The U used classes take cb = ceil(log2 U)
+// bits each (at least 1); a d-gram's packed code is its classes
+// concatenated, the first one in the most significant bits, so packed codes
+// sort like the paths and BFS numbers the depth-d nodes in code order. A byte
+// of the "other" class gets the code U when U < 2^cb (no path contains it),
+// else a separate flag (other_check). Tables:
+//  - filter of depth F (shared memory): bit `code` set iff the F-gram spells
+//    a root path; F <= shortest pattern, so a clear bit proves that nothing
+//    matches at that position;
+//  - deep level of depth D (global memory, read through L2): the root paths
+//    of depth D as uint2 {bits, base} per 32 packed codes; D <= shortest
+//    pattern, so a D-gram that is not a path rules the position out, and
+//    otherwise the walk starts at node deep_first + base + popc(...).
 constexpr uint32_t kBloomK = 2;
 constexpr uint32_t kBloomMul = 0x9E3779B1u;  // Knuth's golden-ratio multiplier
 struct BloomProbe {
@@ -75,15 +87,15 @@ __host__ __device__ inline BloomProbe bloom_probe(uint32_t x, uint32_t gram, uin
     return {h >> (32u - word_bits), bloom_mask(h)};
 }
 
-// Filter of level k and width W (shared memory): a bitset of C^k * W bits.
-// For a k-gram spelling a root path and a next class c_k, the bit
-//   code*W + (c_k mod W)                         (C < 256), or
-//   ((c_k mod W) << 8k) | sum_j b_j << 8j        (byte alphabet, the path
-//                                                 read little-endian)
-// is set iff the depth-k node has a child of some class congruent to c_k
-// mod W; bits of k-grams that are not root paths are clear. It is exact
-// when C <= W. With k < shortest pattern, a clear bit proves that the walk
-// from this start position stops at depth <= k without a match.
+// Filter of level k and width W (byte alphabet, k < kBloomK; shared
+// memory): a bitset of 256^k * W bits. For a k-gram spelling a root path and
+// a next byte c_k, the bit ((c_k mod W) << 8k) | sum_j b_j << 8j (the path
+// read little-endian) is set iff the depth-k node has a child of some byte
+// congruent to c_k mod W; bits of k-grams that are not root paths are clear.
+// It is exact when W >= 256. With k < shortest pattern, a clear bit proves
+// that the walk from this start position stops at depth <= k without a
+// match.
+//
 // Device form of the CRS matrix. BFS numbering makes the next state of
 // non-zero e equal to e + 1, so the value array is implicit, and each row is
 // described by one 16-byte record read in a single load per walk step:
@@ -109,10 +121,11 @@ struct TrieDev {
     uint32_t min_len;                                     // shortest pattern (>= 1)
     uint32_t max_len;
     uint32_t dense_k_max;                                 // deepest filter level
+    uint32_t cb;                                          // byte classes: bits per class
+    uint32_t other_check;                                 // byte classes: U == 2^cb
     const uint2 *deep;                                    // deep level {bits, base} (or null)
-    uint32_t deep_k;                                      // its depth (0: none)
-    uint32_t deep_U;                                      // its code base: used classes
-    uint32_t deep_first;                                  // BFS id of the first depth-deep_k node
+    uint32_t deep_k;                                      // its depth D (0: none)
+    uint32_t deep_first;                                  // BFS id of the first depth-D node
     uint32_t deep_words;                                  // uint2 entries
     const int4 *minfo;                                    // per pattern id (all-matches)
     // Bitmapped nodes (Section III, Fig. 3): node v's children as a 256-bit
@@ -133,17 +146,23 @@ struct HostTrie {
     std::vector<int32_t> nfinal;
     std::vector<uint32_t> depth;
     uint8_t cls[256];
+    // byte classes: per byte its packed class, | 0x80 for a byte of the
+    // "other" class (its class bits are then U, or 0 with other_check)
+    uint8_t lut[256];
+    uint32_t cb = 0, other_check = 0;
     uint32_t C = 0;
     uint32_t min_len = 0, max_len = 0;
     uint64_t n_patterns = 0, n_duplicates = 0;
     uint32_t dense_k_max = 0;
-    uint32_t deep_k = 0, deep_U = 0, deep_first = 0;
-    std::vector<uint32_t> deep;  // interleaved {bits, base} over deep_U^deep_k codes
+    uint32_t deep_k = 0, deep_first = 0;
+    std::vector<uint32_t> deep;  // interleaved {bits, base} over 2^(cb * deep_k) codes
     // all-matches: per input pattern id (distinct patterns only, others -1/0):
     // the next shorter pattern on its root path, its length, and the number
     // of patterns on its root path (itself included)
     std::vector<int32_t> chain, plen, mcnt;
     std::vector<uint32_t> dense[kMaxDenseK + 1];     // interleaved {bits, base}
+    // byte alphabet: filter of level k and width index w; byte classes: the
+    // packed filter of depth F in filter[F][0]
     std::vector<uint32_t> filter[kMaxDenseK + 1][kFilterWidths];
     uint32_t first[kMaxDenseK + 1] = {};
     uint32_t nlevel[kMaxDenseK + 1] = {};
@@ -195,6 +214,14 @@ int launch_matches(const TrieDev &t, const int32_t *ids, uint64_t len, void *wor
 // Enqueues the scan (counts zeroed first). Returns PM_OK / PM_ERR_CUDA.
 int launch_scan(const TrieDev &t, const pm_config &cfg, const ScanArgs &a,
                 void *stream, int device_sms, std::string &msg);
+
+// Shared-memory layout of the scan kernel for a configuration (byte
+// offsets), and the neighbour chunks a lane's window takes (byte classes).
+struct ScanLayout {
+    uint32_t off_lut, off_warp, warp_bytes, off_queue, off_stages, stage_bytes, total;
+    uint32_t filt_u4, filt_words, halo, nnb;
+};
+ScanLayout scan_layout(const TrieDev &t, const pm_config &cfg);
 
 // Dynamic shared memory the scan needs for a configuration.
 uint64_t scan_smem_bytes(const TrieDev &t, const pm_config &cfg);

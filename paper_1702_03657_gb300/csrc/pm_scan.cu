@@ -1,49 +1,50 @@
 // PFAC scan kernels for sm_103a (Section II-C: one failure-less walk per
 // start position over the CRS trie of Section III).
 //
-// One persistent, warp-specialized kernel serves the single-text and the
-// batched scan; one 1024-thread CTA per SM. After the CTA loads the shared
-// tables (its only CTA-wide barrier), its warps split in two.
-//
-// Producer warps, each an independent pipeline over its own text tiles:
+// One persistent kernel serves the single-text and the batched scan, one CTA
+// per SM. After the CTA loads its shared-memory filter (its only CTA-wide
+// barrier), every warp is an independent pipeline over its own text tiles:
 //  a1 staging   lane 0 streams tile + halo (>= longest pattern) into one of
 //               `stages` shared-memory buffers with a 1-D TMA bulk copy
 //               completing on an mbarrier, `stages` tiles ahead (text whose
 //               base is not 16-byte aligned is staged with plain loads);
-//  a2 filter    four consecutive positions per lane: a blocked Bloom probe
-//               of each 4-gram (byte alphabet) or an exact test of each
-//               (k+1)-gram of byte classes, in shared memory; a position
-//               that fails cannot match (every pattern is longer);
-//     start     a passing position's depth-k node from the dense bitmap +
-//               rank table (shared memory); byte-class tries also look up
-//               the deep level's bitmap + rank table in L2, settling most
-//               positions there;
-//  a4 -1        every position gets -1 (one 16-byte streaming store per
-//               lane); walks that match patch their id later;
-//     hand-off  each remaining walk {position, start depth, start node,
-//               text} goes to a shared-memory ring (ballot/popc compaction,
-//               per-cell sequence numbers).
-// Walker warps take up to 32 ring entries at a time, one walk per lane:
-//  a3 CRS walk  each step reads the node's 16-byte row record (row start,
-//               length, has-match bit, first eight column bytes) with the
-//               next text byte; the child of non-zero e is node e + 1 (BFS
-//               order); longer rows are searched in the column array. With
-//               layout 1 the walk reads the bitmapped nodes of Section III
-//               instead (256-bit child bitmap + first child, rank gives the
-//               child);
+//  a2 filter    P consecutive start positions per lane (P = 4 or 8):
+//               byte alphabet: a blocked Bloom probe of each position's
+//                 4-gram (or an exact test of short grams) in shared memory;
+//               byte classes: each lane packs the classes of its P bytes
+//                 (cb bits each, from a lane-replicated table), takes its
+//                 neighbours' packed classes by warp shuffles, and tests each
+//                 position's F-gram in an exact shared-memory bitmap, then
+//                 the D-gram of each passing position in the deep level's
+//                 bitmap (L2);
+//               a position that fails cannot match (F, D and the Bloom gram
+//               are at most the shortest pattern);
+//  a4 -1        every position gets -1 (16-byte streaming stores);
+//     queue     each remaining walk (start position, how it starts) goes to
+//               the warp's own queue in shared memory (ballot/popc
+//               compaction, no atomics); whenever 32 are queued the warp runs
+//               them as one round, one walk per lane;
+//  a3 CRS walk  a walk first resolves its start node (the dense table of
+//               level k, the deep level's rank, or the root), then reads each
+//               node's 16-byte row record (row start, length, has-match bit,
+//               first eight column bytes) with the next text byte; the child
+//               of non-zero e is node e + 1 (BFS order); longer rows are
+//               searched in the column array. With layout 1 the walk reads
+//               the bitmapped nodes of Section III instead (256-bit child
+//               bitmap + first child, rank gives the child);
 //  a4 emit      ids[i] = best[v], count += nfinal[v] of the deepest node v;
+//               the queue's rounds run in the warp that wrote the -1, after a
+//               __syncwarp, so the patch lands after it;
 //  a5 reduce    per-lane counts, warp shuffle reduction, one atomic per warp
 //               (per match and text in batch mode).
 //
-// Every wait (mbarriers, ring cells, idle walkers) is bounded by a clock
-// budget counted from the last progress; on expiry the warp records
-// PM_ERR_TIMEOUT in a device word, waits (bounded) for its copies in flight
-// and returns. The checked variant bounds-checks every shared and global
-// index and records PM_ERR_BOUNDS instead of touching memory out of range.
+// Every mbarrier wait is bounded by a clock budget (pm_config.wait_clocks,
+// default about 2 s); on expiry the warp records PM_ERR_TIMEOUT in a device
+// word, waits with the full budget for its copies in flight and stops. The
+// checked variant bounds-checks every shared and global index and records
+// PM_ERR_BOUNDS instead of touching memory out of range.
 #include <cuda_runtime.h>
 
-#include <atomic>
-#include <cstdio>
 #include <map>
 #include <mutex>
 
@@ -58,8 +59,20 @@ namespace {
 constexpr long long kWaitBudget = 4000000000LL;  // SM clocks (~2 s)
 constexpr uint32_t kSuspendHintNs = 1000000u;      // 1 ms per try_wait
 constexpr int kMaxStages = 4;
+constexpr uint32_t kQueue = 64;                    // walk queue entries per warp
+constexpr uint32_t kFull = 0xffffffffu;
+constexpr int kMaxNeighbours = 8;                  // byte classes: chunks a window takes
+constexpr uint32_t kStagePad = 16;                 // bytes past tile + halo a lane may read
+constexpr uint32_t kWarpHeader = 32;               // mbarriers of a warp's block
 
 enum Mode { MODE_FAST = 0, MODE_CHECKED = 1, MODE_LOOKUPS = 2 };
+
+// How a queued walk starts (bits 61..62 of its position word): from the
+// root; from the depth-k node of the byte alphabet's dense table; from the
+// depth-D node of the byte classes' deep level. The code word holds the
+// k-gram or D-gram for the last two.
+enum WalkKind : uint32_t { WALK_ROOT = 0, WALK_DENSE = 1, WALK_DEEP = 2 };
+constexpr unsigned long long kPosMask = (1ull << 40) - 1;
 
 struct KParams {
     TrieDev t;
@@ -73,32 +86,32 @@ struct KParams {
     int64_t *counts;
     unsigned long long *lookups;
     uint32_t *tile_counts;      // single text, optional: matches per position tile
-    unsigned long long *walks;  // optional: walks queued
-    const uint32_t *filter;     // filter table of level k, width W (global)
-    const uint2 *dense;         // dense table of level k (k >= 1, global)
-    uint32_t first_k;           // BFS id of the first depth-k node
-    uint32_t ck1;               // C^(k-1) (k >= 1): weight of a k-gram's first class
-    uint32_t kload;             // byte classes: classes a group reads (k or deep_k, + 4)
-    uint32_t uk1;               // U^(deep_k - 1): weight of a deep gram's first class
-    uint32_t deep_on;           // look up the deep level before walking
-    uint32_t gram;              // bytes the filter tests per position (k+1 or k+2)
+    unsigned long long *walks;  // optional: walks run
+    const uint32_t *filter;     // source of the shared-memory filter (or null)
+    const uint2 *dense;         // byte alphabet: dense table of level k (global)
+    uint32_t first_k;           // byte alphabet: BFS id of the first depth-k node
+    uint32_t gram;              // bytes the filter tests per position
+    uint32_t cb;                // byte classes: bits per class
+    uint32_t F;                 // byte classes: filter depth (0: none)
+    uint32_t D;                 // byte classes: deep level depth (0: not used)
+    uint32_t nnb;               // byte classes: neighbour chunks a lane's window takes
     uint32_t tile;
     uint32_t halo;
     uint32_t k;
-    uint32_t lw;                // log2 W
+    uint32_t lw;                // log2 W (byte alphabet)
     uint32_t binary;
     uint32_t bitmap;            // walks read bitmapped nodes instead of row records
     uint32_t stages;
-    uint32_t walkers;           // walker warps per CTA (the rest produce)
     uint32_t aligned;
     uint32_t ids_aligned;
+    long long wait_budget;      // SM clocks per TMA wait
     // shared-memory layout (byte offsets)
-    uint32_t off_dense, off_lut, off_ring, off_warp;  // shared tables and ring, then per-warp blocks
-    uint32_t warp_bytes;          // bytes of one producer warp's block
-    uint32_t off_stages;          // inside a warp's block (after its mbarriers)
-    uint32_t stage_bytes;         // tile + halo
+    uint32_t off_lut, off_warp;   // class table, then the per-warp blocks
+    uint32_t warp_bytes;          // bytes of one warp's block
+    uint32_t off_queue;           // inside a warp's block (after its mbarriers)
+    uint32_t off_stages;          // inside a warp's block (after its queue)
+    uint32_t stage_bytes;         // tile + halo + pad
     uint32_t filt_u4;             // filter size in 16-byte units
-    uint32_t dense_u4;            // dense table size in 16-byte units (0: none)
     uint32_t filt_words;          // filter size in u32 words
 };
 
@@ -140,12 +153,12 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t phase)
     return done != 0;
 }
 
-// Bounded wait: false if the phase did not complete within the budget.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t phase)
+// Bounded wait: false if the phase did not complete within `budget` clocks.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t phase, long long budget)
 {
-    long long t0 = clock64();
+    const long long t0 = clock64();
     while (!mbar_try_wait(bar, phase)) {
-        if (clock64() - t0 > kWaitBudget) return false;
+        if (clock64() - t0 > budget) return false;
     }
     return true;
 }
@@ -221,8 +234,8 @@ __device__ __forceinline__ uint32_t ld_trie_u8(const void *ptr, uint64_t pol)
 __device__ __forceinline__ unsigned long long tile_bytes(const KParams &p, unsigned long long t0,
                                                          unsigned long long end)
 {
-    unsigned long long want = (unsigned long long)p.tile + p.halo;
-    unsigned long long left = end - t0;
+    const unsigned long long want = (unsigned long long)p.tile + p.halo;
+    const unsigned long long left = end - t0;
     return left < want ? left : want;
 }
 
@@ -232,8 +245,8 @@ __device__ __forceinline__ void issue_tile(const KParams &p, uint8_t *stages, ui
                                            uint32_t s, unsigned long long t0,
                                            unsigned long long end)
 {
-    uint32_t nb = (uint32_t)tile_bytes(p, t0, end);
-    uint32_t nb16 = nb & ~15u;
+    const uint32_t nb = (uint32_t)tile_bytes(p, t0, end);
+    const uint32_t nb16 = nb & ~15u;
     if (p.aligned && nb16) {
         mbar_arrive_tx(&bars[s], nb16);
         tma_load_1d(stages + (size_t)s * p.stage_bytes, p.text + t0, nb16, &bars[s]);
@@ -249,34 +262,11 @@ __device__ __forceinline__ uint32_t find_text(const uint64_t *off, uint32_t ntex
 {
     uint32_t lo = 0, hi = ntexts;  // answer in [lo, hi)
     while (hi - lo > 1) {
-        uint32_t mid = (lo + hi) >> 1;
+        const uint32_t mid = (lo + hi) >> 1;
         if (__ldg(off + mid) <= pos) lo = mid;
         else hi = mid;
     }
     return lo;
-}
-
-// Walk ring, in shared memory, between the producer warps (tiles, filter)
-// and the walker warps (CRS walks). An entry is one walk (walk_entry_of):
-// x = start position (low 32 bits), y = its bits 32..39 | start depth << 8,
-// z = start node, w = text index (batch) or 0xFFFFFFFF.
-// Each cell carries a sequence number (a bounded multi-producer,
-// multi-consumer ring): cell i starts at i; the producer of slot s waits for
-// s, fills the cell and sets s+1; the walker of slot s waits for s+1, takes
-// the entry and sets s+kRing, freeing the cell for slot s+kRing only.
-constexpr uint32_t kRing = 512;  // entries (power of two)
-
-struct Ring {
-    unsigned int wr;        // slots reserved by producers
-    unsigned int rd;        // slots taken by walkers
-    unsigned int pdone;     // producer warps finished
-    unsigned int progress;  // tiles finished by producers (walkers' heartbeat)
-};
-
-// Bounded spin: true while the budget lasts (a few seconds of SM clocks).
-__device__ __forceinline__ bool spin_ok(long long t0)
-{
-    return clock64() - t0 < kWaitBudget;
 }
 
 // Position of byte b in the CRS row [r0, r0 + deg) whose first eight bytes
@@ -329,14 +319,6 @@ __device__ __forceinline__ uint32_t rel_end_of(unsigned long long e, unsigned lo
     return r > 0xFFFFFFFFull ? 0xFFFFFFFFu : (uint32_t)r;
 }
 
-// Class of byte b from the lane-replicated LUT (identity for the byte alphabet).
-template <bool IDENT>
-__device__ __forceinline__ uint32_t class_of(const uint32_t *s_lut, uint32_t lane, uint32_t b)
-{
-    if (IDENT) return b;
-    return (s_lut[(b >> 2) * 32 + lane] >> ((b & 3) * 8)) & 0xFFu;
-}
-
 // A walk from position pos ended at node v after matching `depth` bytes;
 // has: v's has-match bit (2: not read). Writes the position's id and adds
 // its count when a pattern ends on the path.
@@ -360,32 +342,51 @@ __device__ __forceinline__ void emit_walk(const KParams &p, unsigned long long p
     }
 }
 
-// A ring entry is one walk: the start position (40 bits), the bytes already
-// matched from it (its start depth: 0, k or the deep level's), the node at
-// that depth, and (batch) the index of its text, or 0xFFFFFFFF if unknown.
-__device__ __forceinline__ uint4 walk_entry_of(unsigned long long pos, uint32_t depth,
-                                               uint32_t node, uint32_t txt)
+// The node at which a rank table (uint2 {bits, base} per 32 codes) places
+// `code`: first + base + set bits below it, or 0xFFFFFFFF if its bit is
+// clear (the gram is not a root path).
+template <int MODE>
+__device__ __forceinline__ uint32_t rank_node(const uint2 *tab, uint32_t words, uint32_t first,
+                                              uint32_t code, uint64_t pol)
 {
-    return make_uint4((uint32_t)pos, ((uint32_t)(pos >> 32) & 0xFFu) | (depth << 8), node, txt);
+    if (MODE == MODE_CHECKED && (code >> 5) >= words) {
+        record_error(PM_ERR_BOUNDS);
+        return 0xFFFFFFFFu;
+    }
+    const uint2 d = ld_trie_u2(tab + (code >> 5), pol);
+    const uint32_t bit = code & 31u;
+    if (!((d.x >> bit) & 1u)) return 0xFFFFFFFFu;
+    return first + d.y + __popc(d.x & ((1u << bit) - 1u));
 }
 
-// Run one walk (Section II-C): from its start node, read each node's row
-// record and the next text byte together, move to the child on that byte,
-// and stop at a mismatch, a leaf or the text end; then patch the
-// position's id when a pattern ends on the path.
+// Run one queued walk (Section II-C): resolve its start node, then read
+// each node's row record and the next text byte together, move to the child
+// on that byte, and stop at a mismatch, a leaf or the text end; then patch
+// the position's id when a pattern ends on the path.
 template <bool BATCH, int MODE>
-__device__ __forceinline__ void run_walk(const KParams &p, uint4 e, unsigned long long end,
-                                         uint64_t pol, unsigned long long &acc,
-                                         unsigned long long &look)
+__device__ __forceinline__ void run_walk(const KParams &p, unsigned long long qp, uint32_t code,
+                                         unsigned long long end, uint64_t pol,
+                                         unsigned long long &acc, unsigned long long &look,
+                                         unsigned long long &nwalk)
 {
     const TrieDev &t = p.t;
-    const unsigned long long pos = ((unsigned long long)(e.y & 0xFFu) << 32) | e.x;
-    uint32_t jo = e.y >> 8;
-    uint32_t v = e.z;
+    const unsigned long long pos = qp & kPosMask;
+    const uint32_t kind = (uint32_t)(qp >> 61) & 3u;
+    uint32_t jo = 0, v = 0;
+    if (kind == WALK_DENSE) {
+        v = rank_node<MODE>(p.dense, t.dense_words[p.k], p.first_k, code, pol);
+        if (v == 0xFFFFFFFFu) return;  // the k-gram is not a root path
+        jo = p.k;
+    } else if (kind == WALK_DEEP) {
+        v = rank_node<MODE>(t.deep, t.deep_words, t.deep_first, code, pol);
+        if (v == 0xFFFFFFFFu) return;
+        jo = t.deep_k;
+    }
+    ++nwalk;
     uint32_t txt = 0;
     unsigned long long tend = end;
     if (BATCH) {
-        txt = e.w != 0xFFFFFFFFu ? e.w : find_text(p.offsets, p.ntexts, pos);
+        txt = find_text(p.offsets, p.ntexts, pos);
         tend = __ldg(p.offsets + txt + 1);
     }
     const uint32_t te = rel_end_of(tend, pos);
@@ -442,115 +443,55 @@ __device__ __forceinline__ void run_walk(const KParams &p, uint4 e, unsigned lon
     emit_walk<BATCH>(p, pos, txt, v, jo, has, acc);
 }
 
-// Walker warp: takes up to 32 ring entries at a time, one walk per lane,
-// until every producer warp has finished and the ring is empty; the wait
-// for entries is bounded, counted from the producers' last progress.
-template <bool BATCH, int MODE>
-__device__ __forceinline__ void walker_loop(const KParams &p, Ring *ring, const uint4 *entries,
-                                            unsigned int *flags, uint32_t NP,
-                                            unsigned long long end, uint32_t lane,
-                                            unsigned long long &acc, unsigned long long &look)
+// Classes of the P bytes at st[o .. o + P), packed msb-first (byte o's class
+// in the top cb bits of a P*cb-bit chunk), from the lane-replicated table
+// (word (b/4)*32 + lane holds the entries of bytes 4*(b/4) .. +3, so lane l
+// always reads bank l); *oth: some byte is of the "other" class.
+template <int P>
+__device__ __forceinline__ uint32_t classify(const uint8_t *st, const uint32_t *s_lut,
+                                             uint32_t lane, uint32_t cb, uint32_t &oth)
 {
-    volatile Ring *vr = ring;
-    volatile unsigned int *vf = flags;
-    const uint64_t pol = policy_evict_last();
-    long long t0 = clock64();
-    uint32_t seen = vr->progress;
-    while (true) {
-        uint32_t base = 0, take = 0;  // take 0xFFFFFFFF: stop
-        if (lane == 0) {
-            while (true) {
-                const uint32_t rd = vr->rd, wr = vr->wr;
-                if ((int32_t)(wr - rd) > 0) {
-                    const uint32_t n = min(32u, wr - rd);
-                    if (atomicCAS(&ring->rd, rd, rd + n) == rd) {
-                        base = rd;
-                        take = n;
-                        break;
-                    }
-                    continue;
-                }
-                if (vr->pdone >= NP) {
-                    __threadfence_block();
-                    if ((int32_t)(vr->wr - vr->rd) <= 0) {
-                        take = 0xFFFFFFFFu;
-                        break;
-                    }
-                    continue;
-                }
-                const uint32_t now = vr->progress;
-                if (now != seen) {
-                    seen = now;
-                    t0 = clock64();
-                } else if (!spin_ok(t0)) {
-                    record_error(PM_ERR_TIMEOUT);
-                    take = 0xFFFFFFFFu;
-                    break;
-                }
-                __nanosleep(64);
-            }
+    uint32_t c = 0, o = 0;
+#pragma unroll
+    for (int w = 0; w < P / 4; ++w) {
+        const uint32_t word = *reinterpret_cast<const uint32_t *>(st + 4 * w);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const uint32_t b = (word >> (8 * j)) & 0xFFu;
+            const uint32_t v = (s_lut[(b >> 2) * 32 + lane] >> ((b & 3u) * 8u)) & 0xFFu;
+            c = (c << cb) | (v & 0x7Fu);
+            o |= v;
         }
-        take = __shfl_sync(0xffffffffu, take, 0);
-        base = __shfl_sync(0xffffffffu, base, 0);
-        if (take == 0xFFFFFFFFu) break;
-        if (lane < take) {
-            const uint32_t slot = base + lane, idx = slot & (kRing - 1);
-            const long long w0 = clock64();
-            bool ok = true;
-            while (vf[idx] != slot + 1u) {  // until the producer has filled it
-                if (clock64() - w0 > kWaitBudget) {
-                    record_error(PM_ERR_TIMEOUT);
-                    ok = false;
-                    break;
-                }
-            }
-            if (ok) {
-                __threadfence_block();
-                const uint4 e = entries[idx];
-                __threadfence_block();
-                vf[idx] = slot + kRing;  // free for the slot one lap later
-                run_walk<BATCH, MODE>(p, e, end, pol, acc, look);
-            }
-        }
-        __syncwarp();
     }
+    oth = o >> 7;
+    return c;
 }
 
-// KF: the filter level k when fixed at compile time (byte alphabet), or -1
-// for a runtime k over byte classes. G: bytes the byte-alphabet Bloom filter
-// tests (3 or 4), 0 when not fixed.
-template <int KF, int G, bool IDENT, bool BATCH, int MODE>
+// KF: the byte alphabet's filter level k (0, 1, 2), or -1 for byte classes.
+// G: bytes the byte alphabet's Bloom filter tests (3 or 4), 0 otherwise.
+// P: start positions per lane and group.
+template <int KF, int G, bool IDENT, bool BATCH, int MODE, int P>
 __global__ void __launch_bounds__(1024, 1) pfac_scan_kernel(const KParams p)
 {
     extern __shared__ __align__(16) uint8_t smem[];
     const TrieDev &t = p.t;
     const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const uint32_t NW = blockDim.x >> 5;
-    const uint32_t NP = NW - p.walkers;  // producer warps; the rest walk
+    constexpr uint32_t GP = 32 * P;  // positions per group
 
     const unsigned long long total = BATCH ? __ldg(p.offsets + p.ntexts) : p.total;
     const unsigned long long end = BATCH ? total : p.limit;
     const unsigned long long ntiles = (total + p.tile - 1) / p.tile;
-    if ((unsigned long long)blockIdx.x * NP >= ntiles) return;
+    if ((unsigned long long)blockIdx.x * NW >= ntiles) return;
 
     uint32_t *s_filt = reinterpret_cast<uint32_t *>(smem);
-    uint2 *s_dense = reinterpret_cast<uint2 *>(smem + p.off_dense);
     uint32_t *s_lut = reinterpret_cast<uint32_t *>(smem + p.off_lut);
-    uint4 *entries = reinterpret_cast<uint4 *>(smem + p.off_ring);
-    unsigned int *flags = reinterpret_cast<unsigned int *>(smem + p.off_ring + kRing * 16);
-    Ring *ring = reinterpret_cast<Ring *>(smem + p.off_ring + kRing * 20);
-
-    // Tables into shared memory, shared by all warps of the CTA.
     {
         const uint4 *src = reinterpret_cast<const uint4 *>(p.filter);
         uint4 *dst = reinterpret_cast<uint4 *>(s_filt);
         for (uint32_t i = tid; i < p.filt_u4; i += blockDim.x) dst[i] = __ldg(src + i);
-        const uint4 *dsrc = reinterpret_cast<const uint4 *>(p.dense);
-        uint4 *ddst = reinterpret_cast<uint4 *>(s_dense);
-        for (uint32_t i = tid; i < p.dense_u4; i += blockDim.x) ddst[i] = __ldg(dsrc + i);
         if (!IDENT) {
-            // class LUT replicated per lane: word (b/4)*32 + lane holds the
-            // classes of bytes 4*(b/4) .. +3, so lane l always hits bank l.
+            // class table replicated per lane (see classify)
             for (uint32_t i = tid; i < 64 * 32; i += blockDim.x) {
                 const uint32_t w = i >> 5;
                 s_lut[i] = (uint32_t)__ldg(t.cls + 4 * w) | ((uint32_t)__ldg(t.cls + 4 * w + 1) << 8) |
@@ -558,31 +499,39 @@ __global__ void __launch_bounds__(1024, 1) pfac_scan_kernel(const KParams p)
                            ((uint32_t)__ldg(t.cls + 4 * w + 3) << 24);
             }
         }
-        for (uint32_t i = tid; i < kRing; i += blockDim.x) flags[i] = i;  // cell i free for slot i
-        if (tid == 0) *ring = Ring{0u, 0u, 0u, 0u};
     }
     __syncthreads();  // the only CTA-wide barrier: warps run independently below
 
-    constexpr uint32_t KFU = KF > 0 ? (uint32_t)KF : 0u;  // KF as unsigned (0 if runtime)
-    const uint32_t k = KF >= 0 ? KFU : p.k;
-    const uint32_t gram = p.gram;
-    unsigned long long acc = 0;   // matches (single text)
-    unsigned long long look = 0;  // lookups (MODE_LOOKUPS)
+    const uint64_t pol = policy_evict_last();
+    unsigned long long acc = 0;    // matches (single text)
+    unsigned long long look = 0;   // lookups (MODE_LOOKUPS)
+    unsigned long long nwalk = 0;  // walks run
+    const unsigned long long gw = (unsigned long long)blockIdx.x * NW + warp;
+    const unsigned long long TW = (unsigned long long)gridDim.x * NW;
+    const unsigned long long my_tiles = gw < ntiles ? (ntiles - 1 - gw) / TW + 1 : 0;
 
-    if (warp >= NP) {
-        walker_loop<BATCH, MODE>(p, ring, entries, flags, NP, end, lane, acc, look);
-    } else {
-        const unsigned long long gw = (unsigned long long)blockIdx.x * NP + warp;
-        const unsigned long long TW = (unsigned long long)gridDim.x * NP;
-        const unsigned long long my_tiles = gw < ntiles ? (ntiles - 1 - gw) / TW + 1 : 0;
-
+    if (my_tiles) {
         uint8_t *wsm = smem + p.off_warp + (size_t)warp * p.warp_bytes;
         uint64_t *bars = reinterpret_cast<uint64_t *>(wsm);
+        unsigned long long *qpos = reinterpret_cast<unsigned long long *>(wsm + p.off_queue);
+        uint32_t *qcode = reinterpret_cast<uint32_t *>(wsm + p.off_queue + 8 * kQueue);
         uint8_t *stages = wsm + p.off_stages;
-        volatile unsigned int *vf = flags;
+        const uint32_t below = (1u << lane) - 1u;
+
+        // the warp's walk queue: entries qh .. qh + qn (mod kQueue)
+        uint32_t qh = 0, qn = 0;
+        auto round = [&](uint32_t n) {  // run the first n (<= 32) queued walks
+            if (lane < n) {
+                const uint32_t idx = (qh + lane) & (kQueue - 1);
+                run_walk<BATCH, MODE>(p, qpos[idx], qcode[idx], end, pol, acc, look, nwalk);
+            }
+            qh += n;
+            qn -= n;
+            __syncwarp();
+        };
 
         const unsigned long long tstride = TW * p.tile;  // text between a warp's tiles
-        if (lane == 0 && my_tiles) {
+        if (lane == 0) {
             for (uint32_t s = 0; s < p.stages; ++s) mbar_init(&bars[s], 1);
             fence_mbar_init();
             const unsigned long long pre = my_tiles < p.stages ? my_tiles : p.stages;
@@ -591,12 +540,15 @@ __global__ void __launch_bounds__(1024, 1) pfac_scan_kernel(const KParams p)
         }
         __syncwarp();
 
-        const uint32_t C = t.C;
-        const uint64_t tpol = policy_evict_last();  // deep-level lookups
         const uint32_t lw = p.lw;
-        const uint32_t wmask = (1u << lw) - 1u;
-        // IDENT: filter bit index = low 8k+lw bits of the little-endian window
+        // byte alphabet, exact levels: filter bit index = low 8k+lw bits of
+        // the little-endian window
+        constexpr uint32_t KFU = KF > 0 ? (uint32_t)KF : 0u;
         const uint32_t imask = KF >= 0 ? (uint32_t)((1ull << (8 * KFU + lw)) - 1ull) : 0u;
+        // byte classes: bits of one lane's chunk, code shifts
+        const uint32_t cb = p.cb, Pcb = P * cb;
+        const uint32_t shF = 32u - cb * p.F, shD = 32u - cb * p.D;  // used only when F, D > 0
+        const uint32_t span = (p.gram > 1 ? p.gram : 1u) - 1u;  // bytes a position's filter reads past it
         bool failed = false;
 
         uint32_t s = 0, phase = 0;            // stage and its mbarrier phase
@@ -606,16 +558,18 @@ __global__ void __launch_bounds__(1024, 1) pfac_scan_kernel(const KParams p)
             const uint32_t nbytes = (uint32_t)tile_bytes(p, t0, end);
             uint8_t *st = stages + (size_t)s * p.stage_bytes;
 
-            const bool ok = __all_sync(0xffffffffu, mbar_wait_bounded(&bars[s], phase));
+            const bool ok = __all_sync(kFull, mbar_wait_bounded(&bars[s], phase, p.wait_budget));
             if (!ok) {
                 if (lane == 0) {
                     record_error(PM_ERR_TIMEOUT);
-                    // copies still in flight: tiles it .. it+stages-1
+                    // copies still in flight: tiles it .. it+stages-1 (full budget)
                     for (unsigned long long j = 0; j < p.stages && it + j < my_tiles; ++j) {
                         const uint32_t sj = (uint32_t)((s + j) % p.stages);
-                        mbar_wait_bounded(&bars[sj], phase ^ (uint32_t)((s + j) >= p.stages));
+                        mbar_wait_bounded(&bars[sj], phase ^ (uint32_t)((s + j) >= p.stages),
+                                          kWaitBudget);
                     }
                 }
+                failed = true;
                 break;
             }
             const uint32_t nb16 = p.aligned ? (nbytes & ~15u) : 0u;
@@ -628,22 +582,26 @@ __global__ void __launch_bounds__(1024, 1) pfac_scan_kernel(const KParams p)
             uint32_t cur = 0;
             unsigned long long text_end = end;
             if (BATCH) {
-                cur = find_text(p.offsets, p.ntexts, t0 + 4 * lane < total ? t0 + 4 * lane : t0);
+                cur = find_text(p.offsets, p.ntexts, t0 + P * lane < total ? t0 + P * lane : t0);
                 text_end = __ldg(p.offsets + cur + 1);
             }
             uint32_t rel_end = rel_end_of(text_end, t0);
-            // groups [lp0, lp0+4) with lp0 + 4 <= fast_n take the fast path
+            // groups [lp0, lp0+P) with lp0 + P <= fast_n take the fast path
             auto fast_bound = [&]() -> uint32_t {
-                const uint32_t r = rel_end >= gram - 1 ? rel_end - (gram - 1) : 0u;
+                const uint32_t r = rel_end >= span ? rel_end - span : 0u;
                 return r < tile_n ? r : tile_n;
             };
             uint32_t fast_n = fast_bound();
             int32_t *idt = p.ids + t0;  // this tile's ids
 
-            const uint32_t iters = (tile_n + 127) >> 7;
+            // byte classes: the lane's chunk of the current group (carried
+            // from the previous group's look-ahead)
+            uint32_t cur_c = 0, cur_o = 0;
+            if (!IDENT) cur_c = classify<P>(st + P * lane, s_lut, lane, cb, cur_o);
+
+            const uint32_t iters = (tile_n + GP - 1) / GP;
             for (uint32_t i = 0; i < iters; ++i) {
-                const uint32_t lp0 = (i << 7) + 4 * lane;
-                const uint32_t *wp = reinterpret_cast<const uint32_t *>(st + lp0);
+                const uint32_t lp0 = i * GP + P * lane;
                 if (BATCH && lp0 < tile_n && t0 + lp0 >= text_end) {
                     while (t0 + lp0 >= text_end) {
                         ++cur;
@@ -653,224 +611,179 @@ __global__ void __launch_bounds__(1024, 1) pfac_scan_kernel(const KParams p)
                     fast_n = fast_bound();
                 }
                 const uint32_t cur0 = cur;  // text of position lp0
-                const uint32_t w0 = wp[0], w1 = wp[1];  // bytes lp0 .. lp0+7 (staged)
-                uint32_t need = 0;   // bit q: position lp0+q passed the filter
-                uint32_t rk[4] = {0u, 0u, 0u, 0u};  // node ranks in the start level
-                uint32_t deepm = 0;  // bit q: position lp0+q starts at the deep level
+                uint32_t need = 0;   // bit q: position lp0+q starts a walk at level k / D
                 uint32_t rootm = 0;  // bit q: position lp0+q is walked from the root
-                if (MODE != MODE_LOOKUPS && lp0 + 4 <= fast_n) {
-                    // Fast path: four positions, all bytes up to lp0+3+gram-1
-                    // inside the text. The filter decides, in shared memory,
-                    // which positions can reach depth k+1.
-                    if (IDENT && KF >= (int)kBloomK) {
-                        // blocked Bloom test of the g-gram at each position
-                        const uint32_t sh = 32u - (8u * KFU + lw - 5u);
-                        const uint32_t gsh = G > 0 ? 32u - 8u * G : 32u - 8u * gram;
+                uint32_t nxt_c = 0, nxt_o = 0;
+                uint64_t X = 0;      // byte classes: packed classes from byte lp0 on
+                bool fast = MODE != MODE_LOOKUPS && lp0 + P <= fast_n;
+                if (!IDENT) {
+                    // look ahead: the lane's chunk of the next group (read
+                    // within the stage buffer; bytes past the staged ones
+                    // only reach codes of positions that take the slow path)
+                    if (lp0 + GP + P <= p.stage_bytes)
+                        nxt_c = classify<P>(st + lp0 + GP, s_lut, lane, cb, nxt_o);
+                    X = (uint64_t)cur_c << (64u - Pcb);
 #pragma unroll
-                        for (int q = 0; q < 4; ++q) {
-                            const uint32_t win = q == 0 ? w0 : __funnelshift_r(w0, w1, 8 * q);
-                            // bytes q .. q+g-1, shifted to the top
-                            const uint32_t h = __umulhi(G == 4 ? win : win << gsh, kBloomMul);
-                            const uint32_t word = h >> sh;
-                            if (MODE == MODE_CHECKED && word >= p.filt_words) {
-                                record_error(PM_ERR_BOUNDS);
-                                continue;
+                    for (int d = 1; d <= kMaxNeighbours; ++d) {
+                        if ((uint32_t)d > p.nnb) break;
+                        const uint32_t src = (lane + d) & 31u;
+                        const uint32_t a = __shfl_sync(kFull, cur_c, src);
+                        const uint32_t b = __shfl_sync(kFull, nxt_c, src);
+                        X |= (uint64_t)(lane + d < 32 ? a : b) << (64u - (d + 1) * Pcb);
+                    }
+                    if (t.other_check &&
+                        __any_sync(kFull, cur_o != 0 || (lane < p.nnb && nxt_o != 0)))
+                        fast = false;  // a byte of no pattern: decide per position
+                }
+                if (fast) {
+                    if (IDENT) {
+                        // bytes lp0 .. lp0 + P + 3 (staged)
+                        uint32_t w[P / 4 + 1];
+#pragma unroll
+                        for (int j = 0; j <= P / 4; ++j)
+                            w[j] = *reinterpret_cast<const uint32_t *>(st + lp0 + 4 * j);
+#define PM_WIN(q) ((q) % 4 == 0 ? w[(q) / 4] : __funnelshift_r(w[(q) / 4], w[(q) / 4 + 1], 8 * ((q) % 4)))
+                        if (KF >= (int)kBloomK) {
+                            // blocked Bloom test of the g-gram at each position
+                            const uint32_t sh = 32u - (8u * KFU + lw - 5u);
+                            const uint32_t gsh = G > 0 ? 32u - 8u * G : 32u - 8u * p.gram;
+#pragma unroll
+                            for (int q = 0; q < P; ++q) {
+                                const uint32_t win = PM_WIN(q);
+                                // bytes q .. q+g-1, shifted to the top
+                                const uint32_t h = __umulhi(G == 4 ? win : win << gsh, kBloomMul);
+                                const uint32_t word = h >> sh;
+                                if (MODE == MODE_CHECKED && word >= p.filt_words) {
+                                    record_error(PM_ERR_BOUNDS);
+                                    continue;
+                                }
+                                // both Bloom bits, each rotated down to bit 0 (the
+                                // funnel shift takes its amount mod 32)
+                                const uint32_t val = s_filt[word];
+                                const uint32_t r = __funnelshift_r(val, val, h) & __funnelshift_r(val, val, h >> 5);
+                                need |= (r & 1u) << q;
                             }
-                            // both Bloom bits, each rotated down to bit 0 (the
-                            // funnel shift takes its amount mod 32)
-                            const uint32_t val = s_filt[word];
-                            const uint32_t r = __funnelshift_r(val, val, h) & __funnelshift_r(val, val, h >> 5);
-                            need |= (r & 1u) << q;
+                        } else if (KF >= 0) {
+#pragma unroll
+                            for (int q = 0; q < P; ++q) {
+                                const uint32_t idx = PM_WIN(q) & imask;
+                                const uint32_t word = idx >> 5;
+                                if (MODE == MODE_CHECKED && word >= p.filt_words) {
+                                    record_error(PM_ERR_BOUNDS);
+                                    continue;
+                                }
+                                need |= ((s_filt[word] >> (idx & 31u)) & 1u) << q;
+                            }
                         }
-                    } else if (IDENT && KF >= 0) {
-#pragma unroll
-                        for (int q = 0; q < 4; ++q) {
-                            const uint32_t x = q == 0 ? w0 : __funnelshift_r(w0, w1, 8 * q);
-                            const uint32_t idx = x & imask;
-                            const uint32_t word = idx >> 5;
-                            if (MODE == MODE_CHECKED && word >= p.filt_words) {
-                                record_error(PM_ERR_BOUNDS);
-                                continue;
-                            }
-                            need |= ((s_filt[word] >> (idx & 31u)) & 1u) << q;
+                        if (KF == 0) {  // no dense level: passing positions walk from the root
+                            rootm = need;
+                            need = 0;
                         }
                     } else {
-                        // byte classes: the k-gram code of position lp0 by
-                        // Horner's rule, then rolled one position at a time
-                        // (drop the first class, append the next); a position
-                        // that passes the filter gets the rank of its depth-k
-                        // node from the dense table
-                        uint32_t cw[4];  // classes of bytes lp0 .. lp0+15, four to a word
+                        // byte classes: the F-gram at each position in the
+                        // exact shared-memory bitmap
+                        uint64_t Xq = X;
 #pragma unroll
-                        for (int w = 0; w < 4; ++w) {
-                            const uint32_t word = w == 0 ? w0 : w == 1 ? w1 : (uint32_t)(4 * w) < p.kload ? wp[w] : 0u;
-                            cw[w] = 0;
-#pragma unroll
-                            for (int b = 0; b < 4; ++b)
-                                cw[w] |= class_of<IDENT>(s_lut, lane, (word >> (8 * b)) & 0xFFu) << (8 * b);
-                        }
-                        // class of byte lp0 + j (j known at compile time)
-#define PM_CLS(j) ((cw[(j) >> 2] >> (8 * ((j) & 3))) & 0xFFu)
-                        uint32_t cd = 0;
-#pragma unroll
-                        for (int j = 0; j < 12; ++j)
-                            if (j < (int)k) cd = cd * C + PM_CLS(j);
-                        // classes k .. k+3: the byte after each position's k-gram
-                        const uint32_t kw = k >> 2;
-                        const uint32_t wa = kw == 0 ? cw[0] : kw == 1 ? cw[1] : kw == 2 ? cw[2] : cw[3];
-                        const uint32_t wb = kw == 0 ? cw[1] : kw == 1 ? cw[2] : cw[3];
-                        const uint32_t nc4 = __funnelshift_r(wa, wb, 8u * (k & 3u));
-#pragma unroll
-                        for (int q = 0; q < 4; ++q) {
-                            const uint32_t nc = (nc4 >> (8 * q)) & 0xFFu;
-                            const uint32_t idx = (cd << lw) | (nc & wmask);
-                            const uint32_t word = idx >> 5;
-                            if (MODE == MODE_CHECKED && word >= p.filt_words) {
+                        for (int q = 0; q < P; ++q) {
+                            if (p.F == 0) {
+                                need |= 1u << q;
+                                continue;
+                            }
+                            const uint32_t code = (uint32_t)(Xq >> 32) >> shF;
+                            Xq <<= cb;
+                            if (MODE == MODE_CHECKED && (code >> 5) >= p.filt_words) {
                                 record_error(PM_ERR_BOUNDS);
-                            } else if ((s_filt[word] >> (idx & 31u)) & 1u) {
-                                if (k == 0) {
-                                    need |= 1u << q;
-                                } else if (MODE == MODE_CHECKED && (cd >> 5) >= p.dense_u4 * 2) {
-                                    record_error(PM_ERR_BOUNDS);
-                                } else {
-                                    const uint2 d = s_dense[cd >> 5];
-                                    const uint32_t bit = cd & 31u;
-                                    if ((d.x >> bit) & 1u) {
-                                        need |= 1u << q;
-                                        rk[q] = d.y + __popc(d.x & ((1u << bit) - 1u));
+                                continue;
+                            }
+                            need |= ((s_filt[code >> 5] >> (code & 31u)) & 1u) << q;
+                        }
+                        if (need) {
+                            if (p.D == 0) {
+                                rootm = need;  // no deep level: walk from the root
+                                need = 0;
+                            } else {
+                                // positions whose D-gram leaves the text walk
+                                // from the root
+#pragma unroll
+                                for (int q = 0; q < P; ++q)
+                                    if (((need >> q) & 1u) && lp0 + q + p.D > rel_end) {
+                                        need &= ~(1u << q);
+                                        rootm |= 1u << q;
+                                    }
+                                if (p.D > p.F && need) {
+                                    // the D-gram's bit in the deep level (L2):
+                                    // all loads issued, then tested
+                                    uint32_t dw[P];
+#pragma unroll
+                                    for (int q = 0; q < P; ++q) {
+                                        dw[q] = 0;
+                                        if (!((need >> q) & 1u)) continue;
+                                        const uint32_t code = (uint32_t)((X << (cb * q)) >> 32) >> shD;
+                                        if (MODE == MODE_CHECKED && (code >> 5) >= t.deep_words) {
+                                            record_error(PM_ERR_BOUNDS);
+                                            need &= ~(1u << q);
+                                            continue;
+                                        }
+                                        dw[q] = ld_trie_u32(t.deep + (code >> 5), pol);
+                                    }
+#pragma unroll
+                                    for (int q = 0; q < P; ++q) {
+                                        const uint32_t code = (uint32_t)((X << (cb * q)) >> 32) >> shD;
+                                        if (((need >> q) & 1u) && !((dw[q] >> (code & 31u)) & 1u))
+                                            need &= ~(1u << q);
                                     }
                                 }
                             }
-                            if (q < 3 && k > 0) cd = (cd - PM_CLS(q) * p.ck1) * C + nc;
-                        }
-                        if (p.deep_on && need) {
-                            // deep level: a flagged position whose first
-                            // deep_k bytes lie in its text looks up its
-                            // deep_k-gram (base U, first class most
-                            // significant) in L2. A byte of the "other" class
-                            // or a gram that is not a root path means no match
-                            // (deep_k < shortest pattern); else the walk
-                            // starts at depth deep_k.
-                            const uint32_t K2 = t.deep_k, U = t.deep_U;
-                            // bit j: the byte at lp0 + j is of the "other" class
-                            // (an exact zero-byte test of class xor U per word,
-                            // its four byte flags gathered by one multiply)
-                            uint32_t om = 0;
-#pragma unroll
-                            for (int w = 0; w < 4; ++w) {
-                                const uint32_t x = cw[w] ^ (U * 0x01010101u);
-                                const uint32_t nz = ((x & 0x7F7F7F7Fu) + 0x7F7F7F7Fu) | x;
-                                const uint32_t zf = (~nz & 0x80808080u) >> 7;  // 1 per zero byte
-                                om |= (((zf * 0x00204081u) >> 21) & 0xFu) << (4 * w);
-                            }
-                            const uint32_t kmask = (1u << K2) - 1u;
-                            // the first position's deep code by Horner's rule,
-                            // the next ones by rolling (classes K2 .. K2+2 enter)
-                            uint32_t cc = 0;
-#pragma unroll
-                            for (int j = 0; j < (int)kDeepMaxK; ++j)
-                                if (j < (int)K2) cc = cc * U + PM_CLS(j);
-                            const uint32_t kw2 = K2 >> 2;
-                            const uint32_t ea = kw2 == 0 ? cw[0] : kw2 == 1 ? cw[1] : kw2 == 2 ? cw[2] : cw[3];
-                            const uint32_t eb = kw2 == 0 ? cw[1] : kw2 == 1 ? cw[2] : cw[3];
-                            const uint32_t enter = __funnelshift_r(ea, eb, 8u * (K2 & 3u));
-                            uint2 d2[4];
-                            uint32_t bits2 = 0;  // 5 bits per position: its code's bit in the word
-                            uint32_t dm = 0;
-#pragma unroll
-                            for (int q = 0; q < 4; ++q) {
-                                const uint32_t cq = cc;
-                                if (q < 3) cc = (cc - PM_CLS(q) * p.uk1) * U + ((enter >> (8 * q)) & 0xFFu);
-                                if (!((need >> q) & 1u) || lp0 + q + K2 > rel_end) continue;
-                                if ((om >> q) & kmask) {
-                                    need &= ~(1u << q);
-                                    continue;
-                                }
-                                if (MODE == MODE_CHECKED && (cq >> 5) >= t.deep_words) {
-                                    record_error(PM_ERR_BOUNDS);
-                                    need &= ~(1u << q);
-                                    continue;
-                                }
-                                bits2 |= (cq & 31u) << (5 * q);
-                                d2[q] = ld_trie_u2(t.deep + (cq >> 5), tpol);
-                                dm |= 1u << q;
-                            }
-#pragma unroll
-                            for (int q = 0; q < 4; ++q) {
-                                if (!((dm >> q) & 1u)) continue;
-                                const uint32_t bit = (bits2 >> (5 * q)) & 31u;
-                                if ((d2[q].x >> bit) & 1u)
-                                    rk[q] = d2[q].y + __popc(d2[q].x & ((1u << bit) - 1u));
-                                else
-                                    need &= ~(1u << q);
-                            }
-                            deepm = dm & need;
-                        }
-#undef PM_CLS
-                    }
-                    if (IDENT && KF >= 1 && need) {
-                        // byte alphabet: the depth-k node of each flagged
-                        // position (its k-gram's code, first byte most
-                        // significant); a k-gram that is not a root path
-                        // (a Bloom false positive) needs no walk
-#pragma unroll
-                        for (int q = 0; q < 4; ++q) {
-                            if (!((need >> q) & 1u)) continue;
-                            const uint32_t x = q == 0 ? w0 : __funnelshift_r(w0, w1, 8 * q);
-                            const uint32_t code = KF == 1 ? (x & 0xFFu) : __byte_perm(x, 0u, 0x4401u);
-                            if (MODE == MODE_CHECKED && (code >> 5) >= p.dense_u4 * 2) {
-                                record_error(PM_ERR_BOUNDS);
-                                need &= ~(1u << q);
-                                continue;
-                            }
-                            const uint2 d = s_dense[code >> 5];
-                            const uint32_t bit = code & 31u;
-                            if ((d.x >> bit) & 1u)
-                                rk[q] = d.y + __popc(d.x & ((1u << bit) - 1u));
-                            else
-                                need &= ~(1u << q);
                         }
                     }
                 } else {
                     // ragged group (tile end, text boundary, last bytes of a
-                    // text): every position that passes the filter, or that
-                    // is too close to its text end to test, is walked from the
-                    // root
-                    for (uint32_t q = 0; q < 4; ++q) {
+                    // text, a byte of no pattern): every position that passes
+                    // the filter, or that is too close to its text end to
+                    // test, is walked from the root
+                    for (uint32_t q = 0; q < P; ++q) {
                         const uint32_t lp = lp0 + q;
                         if (lp >= tile_n) break;
-                        const unsigned long long pos = t0 + lp;
                         if (BATCH) {
-                            while (pos >= text_end) {
+                            while (t0 + lp >= text_end) {
                                 ++cur;
                                 text_end = __ldg(p.offsets + cur + 1);
                             }
                             rel_end = rel_end_of(text_end, t0);
                             fast_n = fast_bound();
                         }
-                        if (MODE == MODE_LOOKUPS || lp + gram > rel_end) {
+                        if (MODE == MODE_LOOKUPS || lp + p.gram > rel_end) {
                             rootm |= 1u << q;
                             continue;
                         }
-                        uint32_t word, bits;
+                        uint32_t word = 0, bits = 0;
                         if (IDENT && KF >= (int)kBloomK) {
                             uint32_t x = 0;
-                            for (uint32_t j = 0; j < gram; ++j) x |= (uint32_t)st[lp + j] << (8 * j);
-                            const BloomProbe b = bloom_probe(x, gram, 8u * KFU + lw - 5u);
+                            for (uint32_t j = 0; j < p.gram; ++j) x |= (uint32_t)st[lp + j] << (8 * j);
+                            const BloomProbe b = bloom_probe(x, p.gram, 8u * KFU + lw - 5u);
                             word = b.word;
                             bits = b.mask;
                         } else if (IDENT && KF >= 0) {
                             uint32_t x = 0;
-                            for (uint32_t j = 0; j <= k; ++j) x |= (uint32_t)st[lp + j] << (8 * j);
+                            for (uint32_t j = 0; j <= KFU; ++j) x |= (uint32_t)st[lp + j] << (8 * j);
                             const uint32_t idx = x & imask;
                             word = idx >> 5;
                             bits = 1u << (idx & 31u);
                         } else {
-                            uint32_t cd = 0;
-                            for (uint32_t j = 0; j + 1 <= k; ++j) cd = cd * C + class_of<IDENT>(s_lut, lane, st[lp + j]);
-                            const uint32_t idx = (cd << lw) | (class_of<IDENT>(s_lut, lane, st[lp + k]) & wmask);
-                            word = idx >> 5;
-                            bits = 1u << (idx & 31u);
+                            if (p.F == 0) {
+                                rootm |= 1u << q;
+                                continue;
+                            }
+                            uint32_t code = 0, oth = 0;
+                            for (uint32_t j = 0; j < p.F; ++j) {
+                                const uint32_t b = st[lp + j];
+                                const uint32_t v = (s_lut[(b >> 2) * 32 + lane] >> ((b & 3u) * 8u)) & 0xFFu;
+                                code = (code << cb) | (v & 0x7Fu);
+                                oth |= v & 0x80u;
+                            }
+                            if (oth) continue;  // a byte of no pattern: no match here
+                            word = code >> 5;
+                            bits = 1u << (code & 31u);
                         }
                         if (MODE == MODE_CHECKED && word >= p.filt_words) {
                             record_error(PM_ERR_BOUNDS);
@@ -879,12 +792,12 @@ __global__ void __launch_bounds__(1024, 1) pfac_scan_kernel(const KParams p)
                         if ((s_filt[word] & bits) == bits) rootm |= 1u << q;
                     }
                 }
-                // every position gets -1 now; the walkers patch the matches
+                // every position gets -1 now; the walks patch the matches
                 if (BATCH && p.out_ids) {
                     // per-text output buffers: each position to its own text's
                     uint32_t c2 = cur0;
                     unsigned long long e2 = __ldg(p.offsets + c2 + 1);
-                    for (uint32_t q = 0; q < 4 && lp0 + q < tile_n; ++q) {
+                    for (uint32_t q = 0; q < P && lp0 + q < tile_n; ++q) {
                         const unsigned long long pos = t0 + lp0 + q;
                         while (pos >= e2) {
                             ++c2;
@@ -892,145 +805,148 @@ __global__ void __launch_bounds__(1024, 1) pfac_scan_kernel(const KParams p)
                         }
                         __stcs(p.out_ids[c2] + (pos - __ldg(p.offsets + c2)), -1);
                     }
-                } else if (p.ids_aligned && lp0 + 4 <= tile_n) {
-                    __stcs(reinterpret_cast<int4 *>(idt + lp0), make_int4(-1, -1, -1, -1));
+                } else if (p.ids_aligned && lp0 + P <= tile_n) {
+#pragma unroll
+                    for (int j = 0; j < P / 4; ++j)
+                        __stcs(reinterpret_cast<int4 *>(idt + lp0) + j, make_int4(-1, -1, -1, -1));
                 } else {
 #pragma unroll
-                    for (int q = 0; q < 4; ++q)
+                    for (int q = 0; q < P; ++q)
                         if (lp0 + q < tile_n) __stcs(idt + lp0 + q, -1);
                 }
-                // warp ballot/popc compaction of the walks into the shared
-                // ring, one entry per walk (position, start depth, node)
+                // the group's walks into the warp's queue (ballot/popc
+                // compaction), or, when more than the queue holds, walked at
+                // once by the lanes that own them
                 const uint32_t work = need | rootm;
-                const uint32_t mg = __ballot_sync(0xffffffffu, work != 0);
-                if (mg) {
-                    // slots: walks ordered by position within the group, then
-                    // by lane; with at most one walk per lane (the common case
-                    // under a selective filter) one ballot gives them all
-                    uint32_t mq[4], off[4], tot = 0;
-                    if (!__any_sync(0xffffffffu, (work & (work - 1u)) != 0)) {
-#pragma unroll
-                        for (int q = 0; q < 4; ++q) {
-                            mq[q] = mg;
-                            off[q] = 0;
-                        }
-                        tot = __popc(mg);
+                if (__any_sync(kFull, work != 0)) {
+                    const uint32_t c = __popc(work);
+                    uint32_t pre, tot;
+                    if (!__any_sync(kFull, c > 1u)) {
+                        const uint32_t b1 = __ballot_sync(kFull, c != 0u);
+                        pre = __popc(b1 & below);
+                        tot = __popc(b1);
                     } else {
+                        uint32_t x = c;
 #pragma unroll
-                        for (int q = 0; q < 4; ++q) {
-                            mq[q] = __ballot_sync(0xffffffffu, (work >> q) & 1u);
-                            off[q] = tot;
-                            tot += __popc(mq[q]);
+                        for (int o = 1; o < 32; o <<= 1) {
+                            const uint32_t y = __shfl_up_sync(kFull, x, o);
+                            if (lane >= (uint32_t)o) x += y;
                         }
+                        pre = x - c;
+                        tot = __shfl_sync(kFull, x, 31);
                     }
-                    uint32_t base = 0;
-                    if (lane == 0) {
-                        base = atomicAdd(&ring->wr, tot);
-                        if (p.walks) atomicAdd(p.walks, (unsigned long long)tot);
-                    }
-                    base = __shfl_sync(0xffffffffu, base, 0);
-                    const uint32_t below = (1u << lane) - 1u;
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        if (!((work >> q) & 1u) || failed) continue;
-                        const uint32_t slot = base + off[q] + __popc(mq[q] & below);
-                        const uint32_t idx = slot & (kRing - 1);
-                        const long long w0c = clock64();
-                        while (vf[idx] != slot) {  // until the cell is free for this slot
-                            if (clock64() - w0c > kWaitBudget) {
-                                record_error(PM_ERR_TIMEOUT);
-                                failed = true;
-                                break;
-                            }
+                    if (qn + tot > kQueue)
+                        while (qn) round(qn < 32u ? qn : 32u);
+                    // entry of position lp0 + q: kind and code
+                    auto entry = [&](uint32_t q, uint32_t &code) -> unsigned long long {
+                        const unsigned long long pos = t0 + lp0 + q;
+                        code = 0;
+                        if ((rootm >> q) & 1u) return pos;
+                        if (IDENT) {
+                            code = KF == 1 ? (uint32_t)st[lp0 + q]
+                                           : ((uint32_t)st[lp0 + q] << 8) | st[lp0 + q + 1];
+                            return pos | ((unsigned long long)WALK_DENSE << 61);
                         }
-                        if (failed) break;
-                        const bool root = (rootm >> q) & 1u;
-                        const bool dp = (deepm >> q) & 1u;
-                        const uint32_t depth = root ? 0u : dp ? t.deep_k : k;
-                        const uint32_t node = root || depth == 0 ? 0u
-                                              : (dp ? t.deep_first : p.first_k) + rk[q];
-                        entries[idx] = walk_entry_of(t0 + lp0 + q, depth, node,
-                                                     BATCH && !root ? cur0 : 0xFFFFFFFFu);
-                        __threadfence_block();  // the -1 store and the entry before the flag
-                        vf[idx] = slot + 1u;
+                        code = (uint32_t)((X << (cb * q)) >> 32) >> shD;
+                        return pos | ((unsigned long long)WALK_DEEP << 61);
+                    };
+                    if (tot > kQueue) {
+                        uint32_t wk = work;
+                        while (wk) {
+                            const uint32_t q = __ffs(wk) - 1;
+                            wk &= wk - 1;
+                            uint32_t code;
+                            const unsigned long long e = entry(q, code);
+                            run_walk<BATCH, MODE>(p, e, code, end, pol, acc, look, nwalk);
+                        }
+                        __syncwarp();
+                    } else {
+                        uint32_t wk = work, slot = qh + qn + pre;
+                        while (wk) {
+                            const uint32_t q = __ffs(wk) - 1;
+                            wk &= wk - 1;
+                            uint32_t code;
+                            const unsigned long long e = entry(q, code);
+                            const uint32_t idx = slot++ & (kQueue - 1);
+                            qpos[idx] = e;
+                            qcode[idx] = code;
+                        }
+                        qn += tot;
+                        __syncwarp();
+                        while (qn >= 32u) round(32u);
                     }
-                    failed = __any_sync(0xffffffffu, failed);
-                    if (failed) break;
                 }
+                cur_c = nxt_c;
+                cur_o = nxt_o;
             }
 
             __syncwarp();  // stage s fully consumed by this warp
-            if (failed) {
-                // drain this warp's copies still in flight (tiles it+1 ..
-                // it+stages-1) before leaving
-                if (lane == 0)
-                    for (unsigned long long j = 1; j < p.stages && it + j < my_tiles; ++j) {
-                        const uint32_t sj = (uint32_t)((s + j) % p.stages);
-                        mbar_wait_bounded(&bars[sj], phase ^ (uint32_t)((s + j) >= p.stages));
-                    }
-                break;
-            }
-            if (lane == 0) {
-                if (it + p.stages < my_tiles) {
-                    fence_proxy_async();
-                    issue_tile(p, stages, bars, s, t0 + ahead, end);
-                }
-                atomicAdd(&ring->progress, 1u);
+            if (lane == 0 && it + p.stages < my_tiles) {
+                fence_proxy_async();
+                issue_tile(p, stages, bars, s, t0 + ahead, end);
             }
             if (++s == p.stages) {
                 s = 0;
                 phase ^= 1u;
             }
         }
-        __syncwarp();
-        if (lane == 0) {
-            __threadfence_block();  // the last reservations before the done count
-            atomicAdd(&ring->pdone, 1u);
-        }
+        if (!failed)
+            while (qn) round(qn < 32u ? qn : 32u);
     }
 
-    // warp reductions: single-text count and lookups
+    // warp reductions: single-text count, lookups and walks
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-        acc += __shfl_xor_sync(0xffffffffu, acc, o);
-        look += __shfl_xor_sync(0xffffffffu, look, o);
+        acc += __shfl_xor_sync(kFull, acc, o);
+        look += __shfl_xor_sync(kFull, look, o);
+        nwalk += __shfl_xor_sync(kFull, nwalk, o);
     }
     if (lane == 0) {
         if (!BATCH && acc) atomicAdd(reinterpret_cast<unsigned long long *>(p.counts), acc);
         if (MODE == MODE_LOOKUPS && look && p.lookups) atomicAdd(p.lookups, look);
+        if (p.walks && nwalk) atomicAdd(p.walks, nwalk);
     }
 }
+#undef PM_WIN
 
 typedef void (*KernelFn)(KParams);
 
-template <int KF, int G, bool IDENT>
+template <int KF, int G, bool IDENT, int P>
 KernelFn pick_mode(bool batch, int mode)
 {
     if (batch) {
         switch (mode) {
-        case MODE_CHECKED: return pfac_scan_kernel<KF, G, IDENT, true, MODE_CHECKED>;
-        case MODE_LOOKUPS: return pfac_scan_kernel<KF, G, IDENT, true, MODE_LOOKUPS>;
-        default: return pfac_scan_kernel<KF, G, IDENT, true, MODE_FAST>;
+        case MODE_CHECKED: return pfac_scan_kernel<KF, G, IDENT, true, MODE_CHECKED, P>;
+        case MODE_LOOKUPS: return pfac_scan_kernel<KF, G, IDENT, true, MODE_LOOKUPS, 4>;
+        default: return pfac_scan_kernel<KF, G, IDENT, true, MODE_FAST, P>;
         }
     }
     switch (mode) {
-    case MODE_CHECKED: return pfac_scan_kernel<KF, G, IDENT, false, MODE_CHECKED>;
-    case MODE_LOOKUPS: return pfac_scan_kernel<KF, G, IDENT, false, MODE_LOOKUPS>;
-    default: return pfac_scan_kernel<KF, G, IDENT, false, MODE_FAST>;
+    case MODE_CHECKED: return pfac_scan_kernel<KF, G, IDENT, false, MODE_CHECKED, P>;
+    case MODE_LOOKUPS: return pfac_scan_kernel<KF, G, IDENT, false, MODE_LOOKUPS, 4>;
+    default: return pfac_scan_kernel<KF, G, IDENT, false, MODE_FAST, P>;
     }
 }
 
-// Byte alphabet (C = 256): k is 0, 1 or 2 and fixed at compile time, and so
-// is the Bloom gram length at k = 2.
-KernelFn pick_kernel(uint32_t C, uint32_t k, uint32_t gram, bool batch, int mode)
+template <int P>
+KernelFn pick_kernel_p(uint32_t C, uint32_t k, uint32_t gram, bool batch, int mode)
 {
     if (C == 256) {
-        if (k == 0) return pick_mode<0, 0, true>(batch, mode);
-        if (k == 1) return pick_mode<1, 0, true>(batch, mode);
-        if (gram == 4) return pick_mode<2, 4, true>(batch, mode);
-        return pick_mode<2, 3, true>(batch, mode);
+        if (k == 0) return pick_mode<0, 0, true, P>(batch, mode);
+        if (k == 1) return pick_mode<1, 0, true, P>(batch, mode);
+        if (gram == 4) return pick_mode<2, 4, true, P>(batch, mode);
+        return pick_mode<2, 3, true, P>(batch, mode);
     }
-    return pick_mode<-1, 0, false>(batch, mode);
+    return pick_mode<-1, 0, false, P>(batch, mode);
+}
+
+// Byte alphabet (C = 256): k is 0, 1 or 2 and fixed at compile time, and so
+// is the Bloom gram length at k = 2. The instrumented lookup-counting kernel
+// always takes four positions per lane.
+KernelFn pick_kernel(uint32_t C, uint32_t k, uint32_t gram, bool batch, int mode, int positions)
+{
+    if (positions == 8 && mode != MODE_LOOKUPS) return pick_kernel_p<8>(C, k, gram, batch, mode);
+    return pick_kernel_p<4>(C, k, gram, batch, mode);
 }
 
 // Per-text count finalisation: counts[t] to the caller's *out[t].
@@ -1042,39 +958,39 @@ __global__ void pm_counts_scatter_kernel(const int64_t *counts, int64_t *const *
 
 uint32_t round16(uint64_t x) { return (uint32_t)((x + 15) & ~15ull); }
 
-struct Layout {
-    uint32_t off_dense, off_lut, off_ring, off_warp, warp_bytes, off_stages, stage_bytes, total;
-    uint32_t filt_u4, dense_u4, filt_words, halo;
-};
-
 int width_index(int32_t bits) { return bits == 8 ? 0 : bits == 16 ? 1 : 2; }
 
-// Shared memory: [filter][dense table][class LUT][walk ring] shared by the CTA, then one
-// block per producer warp: [mbarriers][stages x (tile + halo)].
-Layout layout(const TrieDev &t, const pm_config &cfg)
+}  // namespace
+
+// Shared memory: [filter][class table] shared by the CTA, then one block per
+// warp: [mbarriers][walk queue][stages x (tile + halo + pad)].
+ScanLayout scan_layout(const TrieDev &t, const pm_config &cfg)
 {
-    Layout L{};
+    ScanLayout L{};
     const uint32_t k = (uint32_t)cfg.dense_k;
-    L.filt_words = t.filter_words[k][width_index(cfg.filter_bits)];
+    const bool ident = t.C == 256;
+    L.filt_words = ident ? t.filter_words[k][width_index(cfg.filter_bits)]
+                         : (k > 0 ? t.filter_words[k][0] : 0u);
     L.filt_u4 = L.filt_words / 4;
     uint32_t off = round16((uint64_t)L.filt_words * 4);
-    L.off_dense = off;
-    L.dense_u4 = k > 0 ? t.dense_words[k] / 2 : 0;  // the walkers' depth-k lookups
-    off += L.dense_u4 * 16;
     L.off_lut = off;
-    if (t.C != 256) off += 64 * 32 * 4;
-    L.off_ring = off;
-    off += kRing * 16 + kRing * 4 + (uint32_t)sizeof(Ring);
-    off = round16(off);
+    if (!ident) off += 64 * 32 * 4;
     L.off_warp = off;
     L.halo = round16(t.max_len > 16 ? t.max_len : 16);
-    L.stage_bytes = (uint32_t)cfg.tile + L.halo;
-    L.off_stages = round16((uint64_t)kMaxStages * 8);
+    L.stage_bytes = (uint32_t)cfg.tile + L.halo + kStagePad;
+    L.off_queue = kWarpHeader;
+    L.off_stages = kWarpHeader + kQueue * 12;
     L.warp_bytes = L.off_stages + (uint32_t)cfg.stages * L.stage_bytes;
-    const uint32_t producers = (uint32_t)(cfg.threads / 32 - cfg.walkers);
-    L.total = off + producers * L.warp_bytes;
+    L.total = off + (uint32_t)(cfg.threads / 32) * L.warp_bytes;
+    // byte classes: neighbour chunks a lane's window needs
+    uint32_t dmax = k;
+    if (!ident && cfg.deep && t.deep_k > dmax) dmax = t.deep_k;
+    const uint32_t P = (uint32_t)cfg.positions;
+    L.nnb = dmax > 1 ? (dmax - 1 + P - 1) / P : 0;
     return L;
 }
+
+namespace {
 
 std::mutex g_attr_mu;
 
@@ -1098,7 +1014,7 @@ std::map<std::pair<const void *, int>, uint32_t> g_smem_set;  // guarded by g_at
 
 uint64_t scan_smem_bytes(const TrieDev &t, const pm_config &cfg)
 {
-    return layout(t, cfg).total;
+    return scan_layout(t, cfg).total;
 }
 
 int launch_scan(const TrieDev &t, const pm_config &cfg, const ScanArgs &a, void *stream,
@@ -1124,8 +1040,12 @@ int launch_scan(const TrieDev &t, const pm_config &cfg, const ScanArgs &a, void 
     if (batch ? a.ntexts == 0 : a.len == 0) return PM_OK;
 
     const int mode = a.lookups ? MODE_LOOKUPS : (cfg.checked ? MODE_CHECKED : MODE_FAST);
-    KernelFn fn = pick_kernel(t.C, (uint32_t)cfg.dense_k, t.gram[cfg.dense_k], batch, mode);
-    Layout L = layout(t, cfg);
+    pm_config c = cfg;
+    if (mode == MODE_LOOKUPS) c.positions = 4;
+    const bool ident = t.C == 256;
+    KernelFn fn = pick_kernel(t.C, (uint32_t)c.dense_k, ident ? t.gram[c.dense_k] : 0u, batch,
+                              mode, c.positions);
+    const ScanLayout L = scan_layout(t, c);
 
     KParams p{};
     p.t = t;
@@ -1140,36 +1060,36 @@ int launch_scan(const TrieDev &t, const pm_config &cfg, const ScanArgs &a, void 
     p.lookups = a.lookups;
     p.tile_counts = batch ? nullptr : a.tile_counts;
     p.walks = a.walks;
-    p.tile = (uint32_t)cfg.tile;
+    p.tile = (uint32_t)c.tile;
     p.halo = L.halo;
-    p.k = (uint32_t)cfg.dense_k;
-    p.lw = cfg.filter_bits == 8 ? 3u : cfg.filter_bits == 16 ? 4u : 5u;
-    p.filter = t.filter[cfg.dense_k][width_index(cfg.filter_bits)];
-    p.dense = cfg.dense_k > 0 ? t.dense[cfg.dense_k] : nullptr;
-    p.first_k = t.first[cfg.dense_k];
-    p.ck1 = 1u;
-    for (int32_t i = 1; i < cfg.dense_k; ++i) p.ck1 *= t.C;
-    p.deep_on = cfg.deep && t.deep_k > 0 && t.C != 256 ? 1u : 0u;
-    p.kload = (uint32_t)cfg.dense_k + 4u;
-    p.uk1 = 1u;
-    for (uint32_t i = 1; i < t.deep_k; ++i) p.uk1 *= t.deep_U;
-    if (p.deep_on && t.deep_k + 4u > p.kload) p.kload = t.deep_k + 4u;
-    p.gram = t.gram[cfg.dense_k];
-    p.binary = cfg.row_search ? 1u : 0u;
-    p.bitmap = cfg.layout == 1 ? 1u : 0u;
-    p.stages = (uint32_t)cfg.stages;
-    p.walkers = (uint32_t)cfg.walkers;
+    p.k = (uint32_t)c.dense_k;
+    p.lw = c.filter_bits == 8 ? 3u : c.filter_bits == 16 ? 4u : 5u;
+    if (ident) {
+        p.filter = t.filter[c.dense_k][width_index(c.filter_bits)];
+        p.dense = c.dense_k > 0 ? t.dense[c.dense_k] : nullptr;
+        p.first_k = t.first[c.dense_k];
+        p.gram = t.gram[c.dense_k];
+    } else {
+        p.filter = c.dense_k > 0 ? t.filter[c.dense_k][0] : nullptr;
+        p.cb = t.cb;
+        p.F = (uint32_t)c.dense_k;
+        p.D = c.deep && t.deep_k > 0 ? t.deep_k : 0u;
+        p.gram = p.F;
+        p.nnb = L.nnb;
+    }
+    p.binary = c.row_search ? 1u : 0u;
+    p.bitmap = c.layout == 1 ? 1u : 0u;
+    p.stages = (uint32_t)c.stages;
     p.aligned = ((uintptr_t)a.text & 15u) == 0;
     p.ids_aligned = ((uintptr_t)a.ids & 15u) == 0;
-    p.off_dense = L.off_dense;
+    p.wait_budget = c.wait_clocks > 0 ? (long long)c.wait_clocks : kWaitBudget;
     p.off_lut = L.off_lut;
-    p.off_ring = L.off_ring;
     p.off_warp = L.off_warp;
     p.warp_bytes = L.warp_bytes;
+    p.off_queue = L.off_queue;
     p.off_stages = L.off_stages;
     p.stage_bytes = L.stage_bytes;
     p.filt_u4 = L.filt_u4;
-    p.dense_u4 = L.dense_u4;
     p.filt_words = L.filt_words;
 
     cudaError_t e;
@@ -1183,7 +1103,7 @@ int launch_scan(const TrieDev &t, const pm_config &cfg, const ScanArgs &a, void 
             msg = std::string("cudaGetDevice: ") + cudaGetErrorString(e);
             return PM_ERR_CUDA;
         }
-        const LaunchKey key{reinterpret_cast<const void *>(fn), L.total, (uint32_t)cfg.threads, dev};
+        const LaunchKey key{reinterpret_cast<const void *>(fn), L.total, (uint32_t)c.threads, dev};
         std::lock_guard<std::mutex> g(g_attr_mu);
         auto it = g_occ.find(key);
         if (it != g_occ.end()) {
@@ -1202,25 +1122,25 @@ int launch_scan(const TrieDev &t, const pm_config &cfg, const ScanArgs &a, void 
                 set = L.total;
             }
             e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                &occ, reinterpret_cast<const void *>(fn), cfg.threads, L.total);
+                &occ, reinterpret_cast<const void *>(fn), c.threads, L.total);
             if (e != cudaSuccess || occ < 1) {
                 msg = "configuration does not fit on an SM (threads " +
-                      std::to_string(cfg.threads) + ", shared " + std::to_string(L.total) + ")";
+                      std::to_string(c.threads) + ", shared " + std::to_string(L.total) + ")";
                 return PM_ERR_INVAL;
             }
             g_occ.emplace(key, occ);
         }
     }
-    if (cfg.ctas_per_sm > 0 && cfg.ctas_per_sm < occ) occ = cfg.ctas_per_sm;
+    if (c.ctas_per_sm > 0 && c.ctas_per_sm < occ) occ = c.ctas_per_sm;
     unsigned long long grid = (unsigned long long)device_sms * occ;
     const unsigned long long known = batch ? a.total_hint : a.len;
     if (known) {
-        const unsigned long long warps = cfg.threads / 32 - cfg.walkers;
-        unsigned long long ntiles = (known + cfg.tile - 1) / cfg.tile;
-        unsigned long long need = (ntiles + warps - 1) / warps;
+        const unsigned long long warps = c.threads / 32;
+        const unsigned long long ntiles = (known + c.tile - 1) / c.tile;
+        const unsigned long long need = (ntiles + warps - 1) / warps;
         if (need < grid) grid = need;
     }
-    fn<<<(unsigned)grid, cfg.threads, L.total, st>>>(p);
+    fn<<<(unsigned)grid, c.threads, L.total, st>>>(p);
     e = cudaGetLastError();
     if (e != cudaSuccess) {
         msg = std::string("scan launch: ") + cudaGetErrorString(e);

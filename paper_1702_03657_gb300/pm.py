@@ -84,7 +84,8 @@ class pm_server_stats(C.Structure):
 class pm_config(C.Structure):
     _fields_ = [(f, C.c_int32) for f in (
         "threads", "tile", "dense_k", "filter_bits", "row_search",
-        "ctas_per_sm", "stages", "checked", "walkers", "deep", "layout")]
+        "ctas_per_sm", "stages", "checked", "positions", "deep", "layout",
+        "wait_clocks")]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

@@ -1,12 +1,14 @@
 """Autotuner for the scan's launch configuration.
 
-Times candidate `pm_config`s (threads per CTA, walker warps, text bytes per
-warp tile, stages in flight, shared-memory filter level and width) on a
-representative device input with CUDA events, keeps the fastest and installs
-it on the handle with pm_set_config. Results can be cached in a JSON file
-keyed by GPU name and trie shape (nodes, longest pattern, alphabet size, and
-the input's size class). Every candidate computes the same bits; only speed
-differs.
+Times candidate `pm_config`s on a representative device input with CUDA
+events, keeps the fastest and installs it on the handle with pm_set_config.
+The knobs: threads per CTA (the largest that fits, and smaller CTAs for
+small inputs), text bytes per warp tile, tiles in flight per warp, start
+positions per lane (4 or 8), the shared-memory filter level (and, for the
+byte alphabet, its width), and the search of a CRS row's byte column
+(linear or binary). Results can be cached in a JSON file keyed by GPU name
+and trie shape (nodes, longest pattern, alphabet size, and the input's size
+class). Every candidate computes the same bits; only speed differs.
 """
 from __future__ import annotations
 
@@ -19,29 +21,30 @@ from . import pm
 
 
 def candidates(trie: pm.Trie, total_bytes: int) -> List[dict]:
+    """Valid configurations to time for an input of `total_bytes` bytes."""
     st = pm.pm_stats(trie)
     base = pm.pm_get_config(trie)
     kmax = st["dense_k_max"]
     ks = sorted({kmax, max(kmax - 1, 0)})
-    out = []
-    for threads, tile, stages, k, bits, share in itertools.product(
-            (1024, 512), (1024, 2048, 4096), (2, 3), ks, (8, 16, 32),
-            ("2", "4", "8", "1/4", "1/2", "7/8")):
-        # walker warps: a few (selective filters) up to most of the CTA
-        # (tries whose filter passes most positions, e.g. DNA alphabets)
-        warps = threads // 32
-        walkers = int(share) if "/" not in share else \
-            warps * int(share[0]) // int(share[2])
-        if walkers >= warps or (share == "8" and walkers in (warps // 2, warps // 4)) or \
-                (share == "4" and walkers == warps // 4):
+    ident = st["alphabet"] == 256
+    widths = (8, 16, 32) if ident else (8,)
+    # small inputs cannot fill large CTAs: smaller ones launch and start faster
+    threads = [base["threads"], 512] + ([256, 128] if total_bytes <= (4 << 20) else [])
+    tiles = (256, 1024, 2048) if total_bytes <= (4 << 20) else (1024, 2048, 4096)
+    out, seen = [], set()
+    for th, tile, stages, k, bits, pos, rs in itertools.product(
+            threads, tiles, (2, 3), ks, widths, (4, 8), (0, 1)):
+        c = dict(base, threads=th, tile=tile, stages=stages, dense_k=k, filter_bits=bits,
+                 positions=pos, row_search=rs, checked=0, ctas_per_sm=0, layout=0,
+                 wait_clocks=0, deep=0 if ident else (1 if st["deep_k"] else 0))
+        key = tuple(sorted(c.items()))
+        if key in seen:
             continue
-        c = dict(base, threads=threads, tile=tile, stages=stages, dense_k=k,
-                 filter_bits=bits, row_search=0, checked=0, ctas_per_sm=0,
-                 walkers=walkers, deep=1 if st["deep_k"] else 0)
         try:
-            pm.pm_set_config(trie, c)  # validates (shared memory, filter exists)
+            pm.pm_set_config(trie, c)  # validates (shared memory, filter, window)
         except pm.PMError:
             continue
+        seen.add(key)
         out.append(c)
     pm.pm_set_config(trie, base)
     return out

@@ -104,40 +104,47 @@ def test_classes_and_dense_levels(lib):
     t = pm.pm_build_host([b"ACGTACGTAC", b"ACGGA" * 3, b"TTTTTTTT"])
     st = pm.pm_stats(t)
     assert st["alphabet"] == 5           # A, C, G, T + any other byte
-    assert 0 <= st["dense_k_max"] < st["min_len"]
+    assert 0 <= st["dense_k_max"] <= st["min_len"]
     t = pm.pm_build_host([bytes([b]) * 3 for b in range(256)])
-    assert pm.pm_stats(t)["alphabet"] == 256
+    st = pm.pm_stats(t)
+    assert st["alphabet"] == 256 and st["dense_k_max"] < st["min_len"]
 
 
-def _deep_words(U, d):
-    w = -(-U ** d // 32)
+def _deep_words(cb, d):
+    w = -(-(1 << (cb * d)) // 32)
     return w + (w & 1)
 
 
 def test_deep_level_selection(lib):
-    """The deep level: byte classes only, depth D2 in [K + 2, min_len - 1],
-    at most depth 13 and 2^26 codes over the used classes; a bitmap with a
-    rank word per 32 codes (8 bytes)."""
+    """Byte classes: U used classes take cb = ceil(log2 U) bits; the packed
+    filter's depth F is at most the shortest pattern and 20 // cb, the deep
+    level's depth D at most the shortest pattern and 26 // cb; the deep level
+    is a bitmap with a rank word per 32 packed codes (8 bytes). The byte
+    alphabet has no deep level."""
     rng = np.random.Generator(np.random.MT19937(1))
 
     def pats(alpha, lo, hi, n):
         return [rng.choice(list(alpha), size=int(rng.integers(lo, hi + 1))).astype(np.uint8).tobytes()
                 for _ in range(n)]
-    # 4 letters, shortest 12: C = 5, K = 7 (5^7 <= 2^17), D2 = 11
+    # 4 letters (cb = 2), shortest 12: F = 10, D = 12
     st = pm.pm_stats(pm.pm_build_host(pats(b"ACGT", 12, 24, 500)))
-    assert (st["alphabet"], st["dense_k_max"], st["deep_k"]) == (5, 7, 11)
-    assert st["deep_bytes"] == 8 * _deep_words(4, 11)
-    # 3 letters, shortest 14: C = 4, K = 8, D2 = 13 (the window's limit)
+    assert (st["alphabet"], st["dense_k_max"], st["deep_k"]) == (5, 10, 12)
+    assert st["deep_bytes"] == 8 * _deep_words(2, 12)
+    # 3 letters (cb = 2), shortest 14: F = 10, D = 13 (26 bits)
     st = pm.pm_stats(pm.pm_build_host(pats(b"xyz", 14, 20, 300)))
-    assert (st["dense_k_max"], st["deep_k"]) == (8, 13)
-    assert st["deep_bytes"] == 8 * _deep_words(3, 13)
-    # 26 letters, shortest 8: C = 27, K = 3, D2 = 5 (26^6 > 2^26)
+    assert (st["dense_k_max"], st["deep_k"]) == (10, 13)
+    assert st["deep_bytes"] == 8 * _deep_words(2, 13)
+    # 26 letters (cb = 5), shortest 8: F = 4, D = 5
     st = pm.pm_stats(pm.pm_build_host(pats(b"abcdefghijklmnopqrstuvwxyz", 8, 16, 500)))
-    assert (st["dense_k_max"], st["deep_k"]) == (3, 5)
-    assert st["deep_bytes"] == 8 * _deep_words(26, 5)
-    # shortest pattern too close to K, and the byte alphabet: none
-    st = pm.pm_stats(pm.pm_build_host(pats(b"ACGT", 8, 12, 200)))
-    assert st["deep_k"] == 0 and st["deep_bytes"] == 0
+    assert (st["dense_k_max"], st["deep_k"]) == (4, 5)
+    assert st["deep_bytes"] == 8 * _deep_words(5, 5)
+    # shortest pattern below the cb limits: F = D = shortest
+    st = pm.pm_stats(pm.pm_build_host(pats(b"ACGT", 6, 12, 200)))
+    assert (st["dense_k_max"], st["deep_k"]) == (6, 6)
+    # two letters (cb = 1), shortest 30: F = 20, D = 26
+    st = pm.pm_stats(pm.pm_build_host(pats(b"ab", 30, 40, 100)))
+    assert (st["dense_k_max"], st["deep_k"]) == (20, 26)
+    # the byte alphabet: none
     st = pm.pm_stats(pm.pm_build_host([bytes(range(256))] + pats(bytes(range(256)), 20, 30, 50)))
     assert st["alphabet"] == 256 and st["deep_k"] == 0
 
@@ -158,14 +165,23 @@ def test_empty_set_and_host_only_scan(lib):
 def test_config_validation(lib):
     t = pm.pm_build_host([b"hello", b"world"])
     cfg = pm.pm_get_config(t)
-    assert cfg["threads"] in (128, 256, 512, 1024) and cfg["tile"] % 128 == 0
+    assert 128 <= cfg["threads"] <= 1024 and cfg["threads"] % 32 == 0
+    assert cfg["tile"] % (32 * cfg["positions"]) == 0
+    assert cfg["deep"] == 1                         # byte classes with a deep level
     pm.pm_set_config(t, cfg)
-    for bad in ({"threads": 100}, {"tile": 1000}, {"dense_k": -1}, {"stages": 9},
-                {"dense_k": 99}, {"filter_bits": 12}, {"deep": 1}, {"deep": 2}):
+    for bad in ({"threads": 100}, {"threads": 1056}, {"tile": 1000}, {"dense_k": -1},
+                {"stages": 9}, {"dense_k": 99}, {"filter_bits": 16}, {"deep": 2},
+                {"positions": 5}, {"positions": 8, "tile": 128}, {"wait_clocks": -1}):
         c = dict(cfg, **bad)
         with pytest.raises(pm.PMError) as e:
             pm.pm_set_config(t, c)
         assert e.value.code == pm.PM_ERR_INVAL
+    tb = pm.pm_build_host([bytes([b, (b + 1) % 256, 7]) for b in range(256)])
+    cb = pm.pm_get_config(tb)
+    assert pm.pm_stats(tb)["alphabet"] == 256 and cb["deep"] == 0
+    for bad in ({"deep": 1}, {"filter_bits": 12}):
+        with pytest.raises(pm.PMError):
+            pm.pm_set_config(tb, dict(cb, **bad))
 
 
 def test_scan_all_host_side(lib):
@@ -200,28 +216,30 @@ def test_scanner_host_side(lib):
 
 def test_autotune_candidates_host(lib):
     """The autotuner's candidates are valid configurations (the library
-    accepts each), distinct, span few to most walker warps, keep the deep
-    level on where the trie has one, and leave the handle's configuration
-    as it was."""
+    accepts each), distinct, span positions per lane, row search, tile and
+    CTA size, keep the deep level on where the trie has one, and leave the
+    handle's configuration as it was."""
     from paper_1702_03657_gb300 import tune
     rng = np.random.Generator(np.random.MT19937(4))
     pats = [rng.choice(list(b"ACGT"), size=int(rng.integers(14, 21))).astype(np.uint8).tobytes()
             for _ in range(400)]
     t = pm.pm_build_host(pats)
     base = pm.pm_get_config(t)
-    cands = tune.candidates(t, 1 << 20)
-    assert len(cands) >= 20
-    assert pm.pm_get_config(t) == base
-    seen = set()
-    for c in cands:
-        pm.pm_set_config(t, c)
-        assert 1 <= c["walkers"] < c["threads"] // 32
-        assert c["deep"] == 1 and c["layout"] == 0
-        seen.add(tuple(sorted(c.items())))
-    assert len(seen) == len(cands)
-    shares = {c["walkers"] / (c["threads"] // 32) for c in cands}
-    assert min(shares) < 0.1 and max(shares) > 0.8
-    pm.pm_set_config(t, base)
+    for total in (1 << 30, 1 << 16):
+        cands = tune.candidates(t, total)
+        assert len(cands) >= 20
+        assert pm.pm_get_config(t) == base
+        seen = set()
+        for c in cands:
+            pm.pm_set_config(t, c)
+            assert c["deep"] == 1 and c["layout"] == 0
+            seen.add(tuple(sorted(c.items())))
+        assert len(seen) == len(cands)
+        for knob in ("positions", "row_search", "tile", "threads", "stages"):
+            assert len({c[knob] for c in cands}) >= 2, knob
+        if total <= (1 << 16):
+            assert min(c["threads"] for c in cands) <= 256
+        pm.pm_set_config(t, base)
 
 
 def test_binding_checks_arguments(lib):

@@ -70,7 +70,7 @@ def assert_same(ids, cnt, o_ids, o_cnt):
 
 def small_cfg(trie, **kw):
     c = pm.pm_get_config(trie)
-    c.update(threads=128, tile=256, stages=2, walkers=1)
+    c.update(threads=128, tile=256, stages=2, positions=4)
     c.update(kw)
     return c
 
@@ -127,7 +127,7 @@ def test_config_sweep():
                                      filter_bits=bits, row_search=rs,
                                      stages=2 + (tile == 128) * 2,
                                      checked=int(threads == 256),
-                                     walkers=1 + (rs + bits // 8) % (threads // 32 - 1))
+                                     positions=(4, 8)[(rs + threads // 128) % 2])
                             try:
                                 pm.pm_set_config(t, c)
                             except pm.PMError:
@@ -185,14 +185,15 @@ def test_degenerate_pattern_sets():
 
 
 @pytest.mark.parametrize("seed,alphabet,npat,lo,hi,deep_k", [
-    (20, 4, 3000, 12, 24, 11), (21, 3, 800, 14, 20, 13), (22, 26, 2000, 8, 16, 5),
+    (20, 4, 3000, 12, 24, 12), (21, 3, 800, 14, 20, 13), (22, 26, 2000, 8, 16, 5),
 ])
 def test_deep_level(seed, alphabet, npat, lo, hi, deep_k):
-    """Byte-class tries whose shortest pattern lies well below the shared-memory
-    levels get a deep level in L2. With it on and off, checked and counting
-    lookups, and with bytes outside the patterns' alphabet in the text, the
-    bits equal the oracle's; a batch of short texts (shorter than the deep
-    level's depth) too."""
+    """Byte-class tries get a packed-class filter in shared memory and a deep
+    level in L2 (depth D at most the shortest pattern). With the deep level
+    on and off, every filter depth, four and eight positions per lane,
+    checked and counting lookups, and with bytes outside the patterns'
+    alphabet in the text, the bits equal the oracle's; a batch of short texts
+    (shorter than the deep level's depth) too."""
     wl = W.random_case(seed, npat, 150_001, alphabet, lo, hi, plant_rate=0.05)
     rng = np.random.Generator(np.random.MT19937(seed))
     text = wl.text.copy()
@@ -208,7 +209,8 @@ def test_deep_level(seed, alphabet, npat, lo, hi, deep_k):
     o_ids, o_cnt, o_look = ot.scan(text)
     assert o_cnt > 0
     for c in (None, dict(cfg, deep=0), dict(cfg, checked=1), small_cfg(t),
-              small_cfg(t, deep=0, dense_k=1), dict(cfg, tile=128, stages=4)):
+              small_cfg(t, deep=0, dense_k=1), dict(cfg, tile=128, stages=4, positions=4),
+              dict(cfg, positions=4), small_cfg(t, dense_k=0)):
         ids, cnt, _ = gpu_scan(t, text, cfg=c)
         assert_same(ids, cnt, o_ids, o_cnt)
     _, _, look = gpu_scan(t, text, lookups=True)
@@ -279,7 +281,7 @@ def test_truncated_levels_settle_positions():
         if pm.pm_stats(t)["deep_k"]:
             ids0, cnt0, walks0 = walks_of(t, wl.text, cfg=dict(pm.pm_get_config(t), deep=0))
             assert_same(ids0, cnt0, o_ids, o_cnt)
-            assert walks0 > 10 * walks
+            assert walks0 > 5 * walks       # the filter alone passes several times as many
 
 
 def test_tiny_config_full():
