@@ -74,6 +74,9 @@ def parse():
     ap.add_argument("--no-layouts", action="store_true")
     ap.add_argument("--serving-requests", type=int, default=10000)
     ap.add_argument("--workload", default="paper", choices=sorted(WORKLOADS))
+    ap.add_argument("--shard-text", action="store_true",
+                    help="under torchrun: shard ONE text over the ranks (each scans its "
+                         "range with a max_len-1 halo through pm_scan_range; strong scaling)")
     ap.add_argument("--text-mib", type=int, default=None,
                     help="text size (the metric is quoted at 256; smaller sizes "
                          "are for profiler captures)")
@@ -258,7 +261,13 @@ def bench_batched(pm, W, torch, reps: int):
     with torch.cuda.graph(g, stream=s):
         pm.pm_scan_batch(trie, tx, off, ids_b, cnt_b)
 
-    # one launch per text
+    # one launch per text, on its own handle tuned for one text of the
+    # median length (the light launch form competes with the persistent one)
+    trie_p = pm.pm_build(wl.patterns)
+    lens = np.diff(off_h)
+    med = int(np.argsort(lens)[len(lens) // 2])
+    tv_med = tx[off_h[med]:off_h[med + 1]]
+    tuned_p = autotune(trie_p, tv_med, None, reps=50)
     ids_l = torch.empty(total, dtype=torch.int32, device="cuda")
     cnt_l = torch.empty(nt, dtype=torch.int64, device="cuda")
     views = [(tx[off_h[t]:off_h[t + 1]], ids_l[off_h[t]:off_h[t + 1]], cnt_l[t:t + 1])
@@ -266,7 +275,7 @@ def bench_batched(pm, W, torch, reps: int):
 
     def loop():
         for tv, iv, cv in views:
-            pm.pm_scan(trie, tv, iv, cv)
+            pm.pm_scan(trie_p, tv, iv, cv)
 
     with torch.cuda.stream(s):
         loop()
@@ -300,10 +309,15 @@ def bench_batched(pm, W, torch, reps: int):
             "per_text_loop_gbps": gb(ms_loop), "per_text_loop_ms": round(ms_loop, 3),
             "per_text_loop_in_graph_gbps": gb(ms_loop_graph),
             "per_text_loop_in_graph_ms": round(ms_loop_graph, 3),
+            "per_text_device_us": round(ms_loop_graph / nt * 1e3, 2),
             "speedup_vs_loop": round(ms_loop / ms_graph, 1),
             "speedup_vs_loop_in_graph": round(ms_loop_graph / ms_graph, 1),
             "mismatches": mism, "matches": int(cnt_b.sum().item()),
-            "tuned_config": tuned["config"], "configs_tried": tuned["tried"]}
+            "tuned_config": tuned["config"], "configs_tried": tuned["tried"],
+            "per_text_tuned_config": tuned_p["config"],
+            "per_text_configs_tried": tuned_p["tried"],
+            "per_text_form": "light" if tuned_p["config"]["light_max"] >= int(lens.max())
+                             else "persistent"}
 
 
 def bench_serving(pm, W, torch, n_req: int, loads=(0.1, 0.25, 0.5, 0.75, 0.9)):
@@ -441,15 +455,36 @@ def main():
 
     desc, def_mib = WORKLOADS[args.workload]
     mib = args.text_mib or def_mib
-    wl = make_workload(W, args.workload, rank, mib)
+    shard = args.shard_text and world > 1
+    # shard mode: every rank draws the same text and scans its own range of
+    # start positions (plus the halo its walks may read); otherwise each rank
+    # scans its own text
+    wl = make_workload(W, args.workload, 0 if shard else rank, mib)
     trie = pm.pm_build(wl.patterns)
     stats = pm.pm_stats(trie)
     cfg = pm.pm_get_config(trie)
-    n = len(wl.text)
+    if shard:
+        from paper_1702_03657_gb300.dist import shard_text, sum_over_ranks
+        n_full = len(wl.text)
+        a, b, limit = shard_text(n_full, int(stats["max_len"]), rank, world)
+        wl.text = np.ascontiguousarray(wl.text[a:limit])
+        n = b - a
+        for flag in ("no_batched", "no_serving", "no_all_matches", "no_streaming", "no_layouts",
+                     "no_cpu_baseline"):
+            setattr(args, flag, True)
+        args.e2e_steps = 0
+    else:
+        n = len(wl.text)
     text = torch.from_numpy(wl.text).cuda()
-    ids = torch.empty(n, dtype=torch.int32, device="cuda")
+    ids = torch.empty(max(n, 1), dtype=torch.int32, device="cuda")
     cnt = torch.empty(1, dtype=torch.int64, device="cuda")
     stream = torch.cuda.current_stream()
+
+    def scan():
+        if shard:
+            pm.pm_scan_range(trie, text, 0, n, text.numel(), ids[:n], cnt)
+        else:
+            pm.pm_scan(trie, text, ids, cnt)
 
     # trie-lookup count (instrumented kernel, outside the timed region) on
     # the first 1 MiB of the text, scaled to the whole text
@@ -460,7 +495,7 @@ def main():
     lookups = int(look.item()) * n // look_n
 
     for _ in range(max(args.warmup, 3)):
-        pm.pm_scan(trie, text, ids, cnt)
+        scan()
     torch.cuda.synchronize()
 
     K = args.steps
@@ -473,7 +508,7 @@ def main():
     torch.cuda.synchronize()
     ev[0].record(stream)
     for i in range(K):
-        pm.pm_scan(trie, text, ids, cnt)
+        scan()
         ev[i + 1].record(stream)
     torch.cuda.synchronize()
     if world > 1:
@@ -483,8 +518,11 @@ def main():
     total_ms = ev[0].elapsed_time(ev[K])
     total_ms = max_over_ranks(total_ms, "cuda")
     count = int(cnt.item())
-
-    gbps = 8.0 * n * world * K / (total_ms / 1e3) / 1e9
+    if shard:
+        count = sum_over_ranks(count, "cuda")   # the one exchange: 8 bytes
+        gbps = 8.0 * n_full * K / (total_ms / 1e3) / 1e9
+    else:
+        gbps = 8.0 * n * world * K / (total_ms / 1e3) / 1e9
     avg_launch_s = statistics.mean(step_ms) / 1e3
     alg_bytes = n + 4 * n + 8                   # text read + int32 ids + count
     achieved = alg_bytes / avg_launch_s / 1e9   # GB/s
@@ -501,25 +539,27 @@ def main():
             "frac": round(achieved / peak, 4), "traffic": traffic, "peak_kind": peak_kind}
 
     # end to end through the C ABI with host buffers (pm_scan_host)
-    h_text = torch.from_numpy(wl.text).pin_memory()
-    h_ids = torch.empty(n, dtype=torch.int32).pin_memory()
-    hn, hi = h_text.numpy(), h_ids.numpy()
-    hc = pm.pm_scan_host(trie, hn, hi)
-    if world > 1:
-        dist.barrier()
-    t0 = time.perf_counter()
-    for _ in range(args.e2e_steps):
+    e2e = None
+    if args.e2e_steps > 0:
+        h_text = torch.from_numpy(wl.text).pin_memory()
+        h_ids = torch.empty(n, dtype=torch.int32).pin_memory()
+        hn, hi = h_text.numpy(), h_ids.numpy()
         hc = pm.pm_scan_host(trie, hn, hi)
-    e2e_s = max(time.perf_counter() - t0, 1e-9)
-    e2e_s = max_over_ranks(e2e_s, "cuda")
-    chunk = 32 << 20
-    nchunks = (n + chunk - 1) // chunk
-    h2d = n + (nchunks - 1) * (stats["max_len"] - 1)
-    d2h = 4 * n + 8 * nchunks
-    e2e = {"value": round(8.0 * n * world * args.e2e_steps / e2e_s / 1e9, 2), "unit": "Gbps",
-           "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-           "api": "pm_scan_host (pinned host text in, host ids + count out)"}
-    assert hc == count, "pm_scan_host count differs from pm_scan"
+        if world > 1:
+            dist.barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            hc = pm.pm_scan_host(trie, hn, hi)
+        e2e_s = max(time.perf_counter() - t0, 1e-9)
+        e2e_s = max_over_ranks(e2e_s, "cuda")
+        chunk = 32 << 20
+        nchunks = (n + chunk - 1) // chunk
+        h2d = n + (nchunks - 1) * (stats["max_len"] - 1)
+        d2h = 4 * n + 8 * nchunks
+        e2e = {"value": round(8.0 * n * world * args.e2e_steps / e2e_s / 1e9, 2), "unit": "Gbps",
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+               "api": "pm_scan_host (pinned host text in, host ids + count out)"}
+        assert hc == count, "pm_scan_host count differs from pm_scan"
 
     # the same scan with walks over the paper's bitmapped nodes (Section III:
     # 256-bit child bitmap + first child, 36 bytes a node) instead of the
@@ -546,13 +586,15 @@ def main():
                         "csr_bytes": int(stats["csr_bytes"])}
 
     # the truncated levels as an exact prefilter: walks queued vs positions
-    wk = torch.zeros(1, dtype=torch.int64, device="cuda")
-    pm.pm_scan_walks(trie, text, ids, cnt, wk)
-    torch.cuda.synchronize()
-    walks = int(wk.item())
-    prefilter = {"walks": walks, "walks_per_position": round(walks / max(n, 1), 6),
-                 "settled_without_walk": round(1.0 - walks / max(n, 1), 6),
-                 "matched_positions_walked": True}
+    prefilter = None
+    if not shard:
+        wk = torch.zeros(1, dtype=torch.int64, device="cuda")
+        pm.pm_scan_walks(trie, text, ids, cnt, wk)
+        torch.cuda.synchronize()
+        walks = int(wk.item())
+        prefilter = {"walks": walks, "walks_per_position": round(walks / max(n, 1), 6),
+                     "settled_without_walk": round(1.0 - walks / max(n, 1), 6),
+                     "matched_positions_walked": True}
 
     # every occurrence (pm_scan_all): the same scan plus the ordered list
     all_matches = None
@@ -578,6 +620,24 @@ def main():
                        "overhead_vs_scan": round(ms_all / (total_ms / K) - 1.0, 4),
                        "api": "pm_scan_all (ids + count + every occurrence, position "
                               "order, longest first)"}
+
+    # every occurrence with host buffers (pm_scan_all_host): only the list
+    # comes back, 16 bytes per occurrence instead of 4 bytes per position
+    all_matches_host = None
+    if not args.no_all_matches and args.e2e_steps > 0:
+        hm = np.zeros((count + 16, 2), dtype=np.int64)
+        hm_t = torch.from_numpy(hm).pin_memory()
+        hm = hm_t.numpy()
+        assert pm.pm_scan_all_host(trie, hn, hm) == count
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            got = pm.pm_scan_all_host(trie, hn, hm)
+        ah_s = max_over_ranks(max(time.perf_counter() - t0, 1e-9), "cuda")
+        assert got == count, "pm_scan_all_host count differs from pm_scan"
+        all_matches_host = {
+            "value": round(8.0 * n * world * args.e2e_steps / ah_s / 1e9, 2), "unit": "Gbps",
+            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 16 * count + 8 * nchunks,
+            "api": "pm_scan_all_host (pinned host text in, host list of every occurrence out)"}
 
     # the same text as a stream of chunks (pm_scanner_*), device-resident
     streaming = None
@@ -653,7 +713,8 @@ def main():
     line = {
         "metric": METRIC, "value": round(gbps, 2), "unit": "Gbps", "n_gpus": world,
         "steps": K, "warmup": args.warmup, "ms_per_step": round(total_ms / K, 5),
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
+        "higher_is_better": True, "scaling": "strong" if shard else "weak",
+        "vs_baseline": None, "dtype": "u8",
         "data": "synthetic",
         "config": {"workload": desc.format(mib=mib), "text_bytes": n,
                    "patterns": int(stats["n_patterns"]),
@@ -661,7 +722,9 @@ def main():
                    "l2": (f"inputs larger than L2 ({mib} MiB text + {4 * mib} MiB ids per "
                           "step), no flush") if 5 * mib > 126 else
                          f"inputs ({5 * mib} MiB) fit in L2: not a roofline claim",
-                   "parallelism": f"text sharded per rank x{world} (independent texts)"},
+                   "parallelism": (f"one text sharded over {world} ranks (pm_scan_range, "
+                                   f"max_len-1 halo, count summed)") if shard else
+                                  f"independent text per rank x{world}"},
         "roofline": dict(roof, **{
                      "algorithmic_bytes_per_launch": alg_bytes,
                      "hbm_term": {"bytes": alg_bytes, "peak_gbs": peak,
@@ -676,6 +739,7 @@ def main():
                                   "rule": "max(hbm bytes / HBM peak, 4 B x oracle lookups / "
                                           "L2 bandwidth) / kernel time"}}),
         "e2e": e2e,
+        "e2e_all_matches_host": all_matches_host,
         "gpu_launches": K,
         "clocks": clocks.summary(),
         "cpu_baseline": cpu,

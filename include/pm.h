@@ -121,6 +121,10 @@ typedef struct {
                           /* clocks; 0: the default, about 2 s. A wait that  */
                           /* runs out records PM_ERR_TIMEOUT (pm_device_error) */
                           /* and ends the scan early                          */
+    int32_t light_max;    /* single texts of at most this many bytes take the */
+                          /* light launch form (small CTAs, no shared tables, */
+                          /* four positions per thread, walks in place); 0:   */
+                          /* never                                            */
 } pm_config;
 
 /* ---- trie construction (Section III, steps I, II, VI and the CRS step) --
@@ -173,6 +177,20 @@ int pm_set_config(pm_trie *h, const pm_config *cfg);
  *         PM_ERR_CUDA (launch failed). */
 int pm_scan(const pm_trie *h, const uint8_t *d_text, uint64_t len,
             pm_result out, pm_stream stream);
+
+/* pm_scan_range: the start positions [start, end) of a device text of which
+ * the bytes d_text[0 .. limit) may be read (end <= limit). Walks from those
+ * positions stop at `limit`, not at `end`: with limit = end + longest
+ * pattern - 1 (clipped to the text), a range of a long text scanned on its
+ * own gives exactly the ids and count that a scan of the whole text gives
+ * for those positions (the overlap rule of Section II-B). That is how a text
+ * is sharded over several GPUs: each rank holds its range plus that halo.
+ * Writes out.ids[0 .. end - start) and *out.count (the occurrences starting
+ * in the range), asynchronously on `stream`. start == end is legal.
+ * Errors: PM_ERR_INVAL (start > end, end > limit, null pointers with
+ * end > start, limit - start >= 2^40), PM_ERR_HOST_ONLY, PM_ERR_CUDA. */
+int pm_scan_range(const pm_trie *h, const uint8_t *d_text, uint64_t start, uint64_t end,
+                  uint64_t limit, pm_result out, pm_stream stream);
 
 /* pm_scan_batch: ntexts texts stored back to back in d_texts; text t is
  * d_texts[d_offsets[t] .. d_offsets[t+1]) with d_offsets a DEVICE array of
@@ -231,6 +249,21 @@ uint64_t pm_scan_all_work_bytes(uint64_t len);
 int pm_scan_all(const pm_trie *h, const uint8_t *d_text, uint64_t len, pm_result out,
                 pm_match *d_matches, uint64_t capacity, void *d_work, uint64_t work_bytes,
                 pm_stream stream);
+
+/* pm_scan_all_host: every occurrence in a HOST text h_text[0..len), listed in
+ * HOST memory: h_matches[0 .. min(count, capacity)) in the order of
+ * pm_scan_all (position, then the longer pattern first) and *h_count = the
+ * total. Only the list comes back (16 bytes per occurrence), not the 4 bytes
+ * per position that pm_scan_host returns. The text is cut into chunks that
+ * overlap by max_len - 1 bytes (Section II-B's overlap rule); copies in,
+ * scans, listings and copies out are pipelined over the handle's two
+ * internal streams with device buffers owned by the handle (shared with
+ * pm_scan_host; the list buffers grow to the largest chunk's list). Pinned
+ * host memory gives full copy speed. Blocks until the list is on the host.
+ * Not reentrant per handle.
+ * Errors: PM_ERR_INVAL, PM_ERR_HOST_ONLY, PM_ERR_NOMEM, PM_ERR_CUDA. */
+int pm_scan_all_host(pm_trie *h, const uint8_t *h_text, uint64_t len, pm_match *h_matches,
+                     uint64_t capacity, uint64_t *h_count);
 
 /* ---- streams of chunks (Section II-B's overlap rule) ---------------------
  * A scanner scans one long text that arrives in chunks (a packet or file

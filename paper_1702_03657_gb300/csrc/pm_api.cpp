@@ -70,6 +70,9 @@ int32_t pick_bits(const pm_trie *h, int32_t k)
     return 0;
 }
 
+// Single texts up to this size take the light launch form by default.
+constexpr int32_t kLightMax = 64 * 1024;
+
 // Thread counts tried for a CTA, largest first (one CTA per SM).
 const int32_t kThreadChoices[] = {1024, 992, 960, 928, 896, 768, 512, 384, 256, 128};
 
@@ -99,6 +102,7 @@ pm_config default_config(const pm_trie *h, int smem_limit)
     c.checked = 0;
     c.layout = 0;
     c.wait_clocks = 0;
+    c.light_max = kLightMax;
     const bool ident = h->host.C == 256;
     c.deep = !ident && h->host.deep_k > 0 ? 1 : 0;
     const uint64_t limit = (uint64_t)smem_limit - 1024;
@@ -110,7 +114,13 @@ pm_config default_config(const pm_trie *h, int smem_limit)
         std::vector<Pref> prefs;
         if (ident && k >= 2) prefs = {{16, 1024}, {8, 2048}, {8, 1024}};
         const int32_t exact = ident ? pick_bits(h, k) : 8;
-        for (int32_t tile : {1024, 2048, 512, 256}) prefs.push_back({exact, tile});
+        // byte classes behind a deep level: 512-byte tiles (a warp spends more
+        // of its time on L2 round trips per tile, shorter tiles keep more
+        // warps streaming)
+        if (c.deep)
+            for (int32_t tile : {512, 1024, 256}) prefs.push_back({exact, tile});
+        else
+            for (int32_t tile : {1024, 2048, 512, 256}) prefs.push_back({exact, tile});
         for (const Pref &pf : prefs) {
             for (int32_t threads : kThreadChoices) {
                 for (int32_t pos : {8, 4}) {
@@ -131,6 +141,7 @@ pm_config default_config(const pm_trie *h, int smem_limit)
     c.threads = 128;
     c.tile = 128;
     c.positions = 4;
+    c.light_max = kLightMax;
     return c;
 }
 
@@ -182,6 +193,10 @@ int validate_config(const pm_trie *h, const pm_config &c, std::string &why)
         why = "wait_clocks must be >= 0";
         return PM_ERR_INVAL;
     }
+    if (c.light_max < 0) {
+        why = "light_max must be >= 0";
+        return PM_ERR_INVAL;
+    }
     if (!window_fits(h, c)) {
         why = "positions x bits per class too wide for the window at this filter and deep level";
         return PM_ERR_INVAL;
@@ -211,6 +226,7 @@ void fill_dev_sizes(pm_trie *h)
     d.deep_first = t.deep_first;
     d.deep_words = (uint32_t)(t.deep.size() / 2);
     d.n_ids = (uint32_t)t.chain.size();
+    d.ch_len = (uint32_t)(t.ch_info.size() / 2);
     for (int k = 0; k <= pm::kMaxDenseK; ++k) {
         d.dense_words[k] = (uint32_t)(t.dense[k].size() / 2);
         d.first[k] = t.first[k];
@@ -239,6 +255,12 @@ int upload(pm_trie *h)
         const uint32_t r0 = t.row_ptr[v], deg = t.row_ptr[v + 1] - r0;
         uint32_t lab[2] = {0, 0};
         for (uint32_t i = 0; i < deg && i < 8; ++i) lab[i >> 2] |= (uint32_t)t.col[r0 + i] << (8 * (i & 3));
+        if (deg == 1 && t.ch_rem[v] >= 2) {
+            // one child, on a unary chain: the edges forced from here and
+            // the chain position ride in the unused label bytes
+            lab[0] |= t.ch_rem[v] << 8;
+            lab[1] = t.ch_pos[v];
+        }
         row[v] = make_uint4(r0, deg | (t.nfinal[v] > 0 ? 1u << 31 : 0u), lab[0], lab[1]);
     }
     for (uint64_t e = 0; e < nnz; ++e)
@@ -265,6 +287,8 @@ int upload(pm_trie *h)
         for (uint32_t e = t.row_ptr[v]; e < t.row_ptr[v + 1]; ++e)
             bm[8 * v + (t.col[e] >> 5)] |= 1u << (t.col[e] & 31);
     }
+    const size_t i_chl = add(t.ch_lab.data(), t.ch_lab.size());
+    const size_t i_chi = add(t.ch_info.data(), 4 * t.ch_info.size());
     const size_t i_bm = add(bm.data(), 32 * n);
     const size_t i_bmf = add(bm_first.data(), 4 * n);
     const size_t none = (size_t)-1;
@@ -301,6 +325,8 @@ int upload(pm_trie *h)
     d.cls = base + parts[i_cls].off;
     d.deep = i_deep == (size_t)-1 ? nullptr : reinterpret_cast<const uint2 *>(base + parts[i_deep].off);
     d.minfo = i_minfo == (size_t)-1 ? nullptr : reinterpret_cast<const int4 *>(base + parts[i_minfo].off);
+    d.ch_lab = base + parts[i_chl].off;
+    d.ch_info = reinterpret_cast<const int2 *>(base + parts[i_chi].off);
     d.bm = reinterpret_cast<const uint4 *>(base + parts[i_bm].off);
     d.bm_first = reinterpret_cast<const uint32_t *>(base + parts[i_bmf].off);
     for (int k = 0; k <= pm::kMaxDenseK; ++k) {
@@ -387,6 +413,69 @@ int scan_common(const pm_trie *h, const uint8_t *d_texts, const uint64_t *d_offs
     return ok();
 }
 
+
+// Host-buffer scans: chunks of kHostChunk start positions, two slots.
+constexpr uint64_t kHostChunk = 32ull << 20;
+
+// The staging buffers and streams of pm_scan_host / pm_scan_all_host,
+// allocated on first use: per slot the chunk's text (+ max_len - 1 bytes),
+// its ids and count; pinned counts on the host.
+int host_staging(pm_trie *h)
+{
+    const uint64_t overlap = h->host.max_len ? h->host.max_len - 1 : 0;
+    const uint64_t slot = (kHostChunk + overlap + 255) & ~255ull;
+    cudaError_t e;
+    if (!h->h_streams[0]) {
+        for (void *&s : h->h_streams) {
+            cudaStream_t st;
+            e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+            if (e != cudaSuccess) return cuda_fail("cudaStreamCreate", e);
+            s = st;
+        }
+    }
+    if (h->hbuf_chunk != slot) {
+        if (h->d_hbuf_text) cudaFree(h->d_hbuf_text);
+        if (h->d_hbuf_ids) cudaFree(h->d_hbuf_ids);
+        if (h->d_hbuf_counts) cudaFree(h->d_hbuf_counts);
+        if (h->h_hbuf_counts) cudaFreeHost(h->h_hbuf_counts);
+        h->d_hbuf_text = nullptr;
+        h->d_hbuf_ids = nullptr;
+        h->d_hbuf_counts = nullptr;
+        h->h_hbuf_counts = nullptr;
+        h->hbuf_chunk = 0;
+        if (cudaMalloc(&h->d_hbuf_text, 2 * slot) != cudaSuccess ||
+            cudaMalloc(&h->d_hbuf_ids, 2 * 4 * kHostChunk) != cudaSuccess ||
+            cudaMalloc(&h->d_hbuf_counts, 2 * 8) != cudaSuccess ||
+            cudaMallocHost(&h->h_hbuf_counts, 8 * 4096) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(PM_ERR_NOMEM, "host-buffer scan staging buffers");
+        }
+        h->hbuf_chunk = slot;
+    }
+    return PM_OK;
+}
+
+// pm_scan_all on one device text at `pos_base` of a longer one: the scan
+// with per-tile match counts, then the listing (positions + pos_base).
+int scan_all_common(const pm_trie *h, const uint8_t *d_text, uint64_t len, uint64_t limit,
+                    int32_t *d_ids, int64_t *d_count, pm_match *d_matches, uint64_t capacity,
+                    void *d_work, pm_stream stream, uint64_t pos_base)
+{
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    const uint64_t ntiles = (len + (1ull << pm::kMatchTileShift) - 1) >> pm::kMatchTileShift;
+    if (len > 0) {
+        cudaError_t e = cudaMemsetAsync(d_work, 0, 4 * ntiles, st);
+        if (e != cudaSuccess) return cuda_fail("cudaMemsetAsync", e);
+    }
+    int rc = scan_common(h, d_text, nullptr, 1, len, limit, d_ids, d_count, nullptr, nullptr,
+                         stream, len > 0 ? static_cast<uint32_t *>(d_work) : nullptr);
+    if (rc != PM_OK || len == 0) return rc;
+    std::string msg;
+    rc = pm::launch_matches(h->dev, d_ids, len, d_work, d_matches, capacity, stream, msg, pos_base);
+    if (rc != PM_OK) return fail(rc, msg);
+    return PM_OK;
+}
+
 }  // namespace
 
 namespace pm {
@@ -424,6 +513,8 @@ void pm_free(pm_trie *h)
     if (h->d_hbuf_ids) cudaFree(h->d_hbuf_ids);
     if (h->d_hbuf_counts) cudaFree(h->d_hbuf_counts);
     if (h->h_hbuf_counts) cudaFreeHost(h->h_hbuf_counts);
+    if (h->d_hbuf_work) cudaFree(h->d_hbuf_work);
+    if (h->d_hbuf_match) cudaFree(h->d_hbuf_match);
     if (h->d_arena) cudaFree(h->d_arena);
     delete h;
 }
@@ -486,6 +577,17 @@ int pm_scan(const pm_trie *h, const uint8_t *d_text, uint64_t len, pm_result out
                        stream);
 }
 
+int pm_scan_range(const pm_trie *h, const uint8_t *d_text, uint64_t start, uint64_t end,
+                  uint64_t limit, pm_result out, pm_stream stream)
+{
+    if (start > end || end > limit)
+        return fail(PM_ERR_INVAL, "range must satisfy start <= end <= limit");
+    if (limit - start >= (1ull << 40)) return fail(PM_ERR_INVAL, "range of 2^40 bytes or more");
+    if (end > start && !d_text) return fail(PM_ERR_INVAL, "text is NULL");
+    return scan_common(h, d_text ? d_text + start : nullptr, nullptr, 1, end - start,
+                       limit - start, out.ids, out.count, nullptr, nullptr, stream);
+}
+
 int pm_scan_walks(const pm_trie *h, const uint8_t *d_text, uint64_t len, int32_t *d_ids,
                   int64_t *d_count, uint64_t *d_walks, const pm_config *cfg, pm_stream stream)
 {
@@ -512,18 +614,108 @@ int pm_scan_all(const pm_trie *h, const uint8_t *d_text, uint64_t len, pm_result
     if (len > 0 && (!d_work || work_bytes < need))
         return fail(PM_ERR_INVAL, "workspace of " + std::to_string(need) + " bytes needed");
     if (((uintptr_t)d_work & 255u) != 0) return fail(PM_ERR_INVAL, "workspace not 256-byte aligned");
-    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-    const uint64_t ntiles = (len + (1ull << pm::kMatchTileShift) - 1) >> pm::kMatchTileShift;
-    if (len > 0 && h->d_arena) {
-        cudaError_t e = cudaMemsetAsync(d_work, 0, 4 * ntiles, st);
-        if (e != cudaSuccess) return cuda_fail("cudaMemsetAsync", e);
+    if (!h->d_arena) return fail(PM_ERR_HOST_ONLY, "handle was built with pm_build_host");
+    const int rc = scan_all_common(h, d_text, len, len, out.ids, out.count, d_matches, capacity,
+                                   d_work, stream, 0);
+    return rc != PM_OK ? rc : ok();
+}
+
+int pm_scan_all_host(pm_trie *h, const uint8_t *h_text, uint64_t len, pm_match *h_matches,
+                     uint64_t capacity, uint64_t *h_count)
+{
+    if (!h) return fail(PM_ERR_INVAL, "handle is NULL");
+    if (!h->d_arena) return fail(PM_ERR_HOST_ONLY, "handle was built with pm_build_host");
+    if (!h_count || (len > 0 && !h_text) || (capacity > 0 && !h_matches))
+        return fail(PM_ERR_INVAL, "text, matches or count is NULL");
+    *h_count = 0;
+    if (len == 0) return ok();
+    int rc = host_staging(h);
+    if (rc != PM_OK) return rc;
+    const uint64_t CH = kHostChunk;
+    const uint64_t overlap = h->host.max_len ? h->host.max_len - 1 : 0;
+    const uint64_t slot = h->hbuf_chunk;
+    const uint64_t wbytes = (pm::match_work_bytes(CH) + 255) & ~255ull;
+    cudaError_t e;
+    if (h->hbuf_work_bytes != wbytes) {
+        if (h->d_hbuf_work) cudaFree(h->d_hbuf_work);
+        h->d_hbuf_work = nullptr;
+        h->hbuf_work_bytes = 0;
+        if (cudaMalloc(&h->d_hbuf_work, 2 * wbytes) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(PM_ERR_NOMEM, "pm_scan_all_host workspace");
+        }
+        h->hbuf_work_bytes = wbytes;
     }
-    int rc = scan_common(h, d_text, nullptr, 1, len, len, out.ids, out.count, nullptr, nullptr,
-                         stream, len > 0 ? static_cast<uint32_t *>(d_work) : nullptr);
-    if (rc != PM_OK || len == 0) return rc;
-    std::string msg;
-    rc = pm::launch_matches(h->dev, out.ids, len, d_work, d_matches, capacity, stream, msg);
-    if (rc != PM_OK) return fail(rc, msg);
+    auto grow = [&](uint64_t need) -> int {
+        uint64_t cap = h->hbuf_mcap ? h->hbuf_mcap : (1ull << 16);
+        while (cap < need) cap *= 2;
+        if (cap == h->hbuf_mcap && h->d_hbuf_match) return PM_OK;
+        for (void *s : h->h_streams) cudaStreamSynchronize(reinterpret_cast<cudaStream_t>(s));
+        if (h->d_hbuf_match) cudaFree(h->d_hbuf_match);
+        h->d_hbuf_match = nullptr;
+        h->hbuf_mcap = 0;
+        if (cudaMalloc(&h->d_hbuf_match, 2 * sizeof(pm_match) * cap) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(PM_ERR_NOMEM, "pm_scan_all_host match buffers");
+        }
+        h->hbuf_mcap = cap;
+        return PM_OK;
+    };
+    rc = grow(1);
+    if (rc != PM_OK) return rc;
+    const uint64_t nchunks = (len + CH - 1) / CH;
+    // Chunk c runs on slot c & 1: text in, scan, listing, count out. Its list
+    // is copied out once its count is known (two chunks in flight); a chunk
+    // whose list outgrew the buffers is run again with larger ones.
+    auto enqueue = [&](uint64_t c) -> int {
+        const int b = (int)(c & 1);
+        cudaStream_t st = reinterpret_cast<cudaStream_t>(h->h_streams[b]);
+        const uint64_t s0 = c * CH;
+        const uint64_t npos = std::min(CH, len - s0);
+        const uint64_t nread = std::min(npos + overlap, len - s0);
+        uint8_t *dt = h->d_hbuf_text + b * slot;
+        e = cudaMemcpyAsync(dt, h_text + s0, nread, cudaMemcpyHostToDevice, st);
+        if (e != cudaSuccess) return cuda_fail("cudaMemcpyAsync H2D", e);
+        int r = scan_all_common(h, dt, npos, nread, h->d_hbuf_ids + b * CH, h->d_hbuf_counts + b,
+                                h->d_hbuf_match + b * h->hbuf_mcap, h->hbuf_mcap,
+                                static_cast<uint8_t *>(h->d_hbuf_work) + b * wbytes,
+                                reinterpret_cast<pm_stream>(st), s0);
+        if (r != PM_OK) return r;
+        e = cudaMemcpyAsync(h->h_hbuf_counts + b, h->d_hbuf_counts + b, 8, cudaMemcpyDeviceToHost, st);
+        if (e != cudaSuccess) return cuda_fail("cudaMemcpyAsync D2H", e);
+        return PM_OK;
+    };
+    uint64_t c_next = 0, c_done = 0, total = 0;
+    while (c_done < nchunks) {
+        while (c_next < nchunks && c_next < c_done + 2) {
+            rc = enqueue(c_next++);
+            if (rc != PM_OK) return rc;
+        }
+        const int b = (int)(c_done & 1);
+        cudaStream_t st = reinterpret_cast<cudaStream_t>(h->h_streams[b]);
+        e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return cuda_fail("cudaStreamSynchronize", e);
+        const uint64_t cnt = (uint64_t)h->h_hbuf_counts[b];
+        if (cnt > h->hbuf_mcap) {
+            rc = grow(cnt);
+            if (rc != PM_OK) return rc;
+            c_next = c_done;  // run this chunk (and the next) again
+            continue;
+        }
+        if (total < capacity && cnt) {
+            const uint64_t n = std::min(cnt, capacity - total);
+            e = cudaMemcpyAsync(h_matches + total, h->d_hbuf_match + b * h->hbuf_mcap,
+                                sizeof(pm_match) * n, cudaMemcpyDeviceToHost, st);
+            if (e != cudaSuccess) return cuda_fail("cudaMemcpyAsync D2H", e);
+        }
+        total += cnt;
+        ++c_done;
+    }
+    for (void *s : h->h_streams) {
+        e = cudaStreamSynchronize(reinterpret_cast<cudaStream_t>(s));
+        if (e != cudaSuccess) return cuda_fail("cudaStreamSynchronize", e);
+    }
+    *h_count = total;
     return ok();
 }
 
@@ -554,37 +746,12 @@ int pm_scan_host(pm_trie *h, const uint8_t *h_text, uint64_t len, int32_t *h_ids
     if (len == 0) return ok();
     // Chunks of CH start positions; each chunk also copies the next
     // overlap = max_len - 1 bytes so that its last walks can finish.
-    const uint64_t CH = 32ull << 20;
+    const uint64_t CH = kHostChunk;
     const uint64_t overlap = h->host.max_len ? h->host.max_len - 1 : 0;
-    const uint64_t slot = (CH + overlap + 255) & ~255ull;
+    int rc0 = host_staging(h);
+    if (rc0 != PM_OK) return rc0;
+    const uint64_t slot = h->hbuf_chunk;
     cudaError_t e;
-    if (!h->h_streams[0]) {
-        for (void *&s : h->h_streams) {
-            cudaStream_t st;
-            e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
-            if (e != cudaSuccess) return cuda_fail("cudaStreamCreate", e);
-            s = st;
-        }
-    }
-    if (h->hbuf_chunk != slot) {
-        if (h->d_hbuf_text) cudaFree(h->d_hbuf_text);
-        if (h->d_hbuf_ids) cudaFree(h->d_hbuf_ids);
-        if (h->d_hbuf_counts) cudaFree(h->d_hbuf_counts);
-        if (h->h_hbuf_counts) cudaFreeHost(h->h_hbuf_counts);
-        h->d_hbuf_text = nullptr;
-        h->d_hbuf_ids = nullptr;
-        h->d_hbuf_counts = nullptr;
-        h->h_hbuf_counts = nullptr;
-        h->hbuf_chunk = 0;
-        if (cudaMalloc(&h->d_hbuf_text, 2 * slot) != cudaSuccess ||
-            cudaMalloc(&h->d_hbuf_ids, 2 * 4 * CH) != cudaSuccess ||
-            cudaMalloc(&h->d_hbuf_counts, 2 * 8) != cudaSuccess ||
-            cudaMallocHost(&h->h_hbuf_counts, 8 * 4096) != cudaSuccess) {
-            cudaGetLastError();
-            return fail(PM_ERR_NOMEM, "pm_scan_host staging buffers");
-        }
-        h->hbuf_chunk = slot;
-    }
     const uint64_t nchunks = (len + CH - 1) / CH;
     int64_t total = 0;
     for (uint64_t c0 = 0; c0 < nchunks; c0 += 4096) {

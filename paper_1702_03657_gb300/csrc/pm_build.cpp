@@ -156,9 +156,11 @@ int build_class_tables(HostTrie &t, uint32_t nn, const std::vector<uint32_t> &lv
     while ((1u << cb) < U) ++cb;
     t.cb = cb;
     t.other_check = U == (1u << cb) ? 1u : 0u;
+    // a byte of no pattern gets the code U when it fits in cb bits (then no
+    // path contains it); otherwise (U == 2^cb, so cb <= 7) bit 7 flags it
     for (int b = 0; b < 256; ++b) {
         const uint32_t c = t.cls[b];
-        t.lut[b] = c < U ? (uint8_t)c : (uint8_t)(0x80u | (t.other_check ? 0u : U));
+        t.lut[b] = c < U ? (uint8_t)c : (uint8_t)(t.other_check ? 0x80u : U);
     }
     const uint32_t FM = m ? std::min<uint32_t>({t.min_len, kFilterCodeBits / cb, (uint32_t)kMaxDenseK}) : 0;
     const uint32_t D = m ? std::min<uint32_t>(t.min_len, kDeepCodeBits / cb) : 0;
@@ -210,6 +212,40 @@ int build_class_tables(HostTrie &t, uint32_t nn, const std::vector<uint32_t> &lv
         t.deep_first = count(D) ? begin(D) : 0;
     }
     return PM_OK;
+}
+
+
+// Unary chains (see pm_internal.h). BFS order visits a chain's first node
+// before the rest of it, so a one-child node not yet on a chain starts one.
+void build_chains(HostTrie &t, uint32_t nn)
+{
+    t.ch_lab.clear();
+    t.ch_info.clear();
+    t.ch_pos.assign(nn, 0);
+    t.ch_rem.assign(nn, 0);
+    std::vector<uint32_t> nodes;
+    for (uint32_t v = 0; v < nn; ++v) {
+        if (t.row_ptr[v + 1] - t.row_ptr[v] != 1 || t.ch_rem[v] != 0) continue;
+        const uint32_t o = (uint32_t)t.ch_lab.size();
+        nodes.clear();
+        uint32_t u = v;
+        while (t.row_ptr[u + 1] - t.row_ptr[u] == 1) {
+            nodes.push_back(u);
+            t.ch_lab.push_back(t.col[t.row_ptr[u]]);
+            t.ch_info.push_back(t.best[u]);
+            t.ch_info.push_back(t.nfinal[u]);
+            u = (uint32_t)t.next[t.row_ptr[u]];
+        }
+        t.ch_lab.push_back(0);
+        t.ch_info.push_back((int32_t)u);
+        t.ch_info.push_back(0);
+        const uint32_t L = (uint32_t)nodes.size();
+        for (uint32_t j = 0; j < L; ++j) {
+            t.ch_pos[nodes[j]] = o + j;
+            t.ch_rem[nodes[j]] = L - j;
+        }
+    }
+    t.ch_lab.resize(t.ch_lab.size() + 32, 0);
 }
 
 int build_host_trie(const uint8_t *const *patterns, const uint32_t *lengths,
@@ -339,6 +375,7 @@ int build_host_trie(const uint8_t *const *patterns, const uint32_t *lengths,
     const uint32_t nn = (uint32_t)rng.size();
     t.level_nodes.assign(t.max_len + 1, 0);
     for (uint32_t v = 0; v < nn; ++v) ++t.level_nodes[t.depth[v]];
+    build_chains(t, nn);
 
     for (int k = 0; k <= kMaxDenseK; ++k) {
         t.dense[k].clear();

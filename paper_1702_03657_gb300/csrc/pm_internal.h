@@ -128,6 +128,11 @@ struct TrieDev {
     uint32_t deep_first;                                  // BFS id of the first depth-D node
     uint32_t deep_words;                                  // uint2 entries
     const int4 *minfo;                                    // per pattern id (all-matches)
+    // Unary chains (see HostTrie): labels and, per chain position, the emit
+    // {best, nfinal} of the node there, or {end node, 0} at a chain's end
+    const uint8_t *ch_lab;
+    const int2 *ch_info;
+    uint32_t ch_len;                                      // chain positions
     // Bitmapped nodes (Section III, Fig. 3): node v's children as a 256-bit
     // bitmap over bytes (two uint4 at bm[2v]) and the id of its first child;
     // the child on byte b is first + (set bits below b)
@@ -146,8 +151,8 @@ struct HostTrie {
     std::vector<int32_t> nfinal;
     std::vector<uint32_t> depth;
     uint8_t cls[256];
-    // byte classes: per byte its packed class, | 0x80 for a byte of the
-    // "other" class (its class bits are then U, or 0 with other_check)
+    // byte classes: per byte its packed class; a byte of the "other" class
+    // gets U, or 0x80 (flag, class bits 0) with other_check
     uint8_t lut[256];
     uint32_t cb = 0, other_check = 0;
     uint32_t C = 0;
@@ -167,6 +172,16 @@ struct HostTrie {
     uint32_t first[kMaxDenseK + 1] = {};
     uint32_t nlevel[kMaxDenseK + 1] = {};
     std::vector<uint32_t> level_nodes;  // nodes per depth, every depth
+    // Unary chains: each maximal run u_0 -> u_1 -> ... -> u_L of nodes with
+    // exactly one child (u_0's parent has another number of children, u_L
+    // has none or several) is stored at positions o .. o+L: ch_lab[o+j] is
+    // the byte of the edge u_j -> u_{j+1}; ch_info[o+j] = {best, nfinal} of
+    // u_j for j < L, and {u_L, 0} at o+L. A one-child node u_j has
+    // ch_pos = o+j and ch_rem = L-j (edges forced from it); other nodes have
+    // ch_rem = 0. ch_lab is padded with 32 zero bytes.
+    std::vector<uint8_t> ch_lab;
+    std::vector<int32_t> ch_info;       // interleaved pairs
+    std::vector<uint32_t> ch_pos, ch_rem;
     uint32_t gram[kMaxDenseK + 1] = {};  // bytes a level-k filter tests: k+1 or k+2
 };
 
@@ -205,11 +220,12 @@ struct ScanArgs {
 
 // All-matches listing after a single-text scan with tile_counts (same
 // stream): lists every occurrence into out[0 .. capacity) in position order,
-// longest pattern first. work: the tile counts then the block sums and
-// offsets (match_work_bytes(len) bytes).
+// longest pattern first, positions offset by pos_base. work: the tile counts
+// then the block sums and offsets (match_work_bytes(len) bytes).
 uint64_t match_work_bytes(uint64_t len);
 int launch_matches(const TrieDev &t, const int32_t *ids, uint64_t len, void *work,
-                   pm_match *out, uint64_t capacity, void *stream, std::string &msg);
+                   pm_match *out, uint64_t capacity, void *stream, std::string &msg,
+                   uint64_t pos_base = 0);
 
 // Enqueues the scan (counts zeroed first). Returns PM_OK / PM_ERR_CUDA.
 int launch_scan(const TrieDev &t, const pm_config &cfg, const ScanArgs &a,
@@ -250,4 +266,8 @@ struct pm_trie {
     int64_t *d_hbuf_counts = nullptr;
     int64_t *h_hbuf_counts = nullptr;  // pinned
     uint64_t hbuf_chunk = 0;
+    // pm_scan_all_host: per slot, the listing workspace and the match list
+    void *d_hbuf_work = nullptr;
+    pm_match *d_hbuf_match = nullptr;
+    uint64_t hbuf_work_bytes = 0, hbuf_mcap = 0;
 };

@@ -94,7 +94,8 @@ __global__ void __launch_bounds__(1024, 1) pm_block_scan_kernel(const unsigned l
 // counts.
 __global__ void __launch_bounds__(1024, 1) pm_matches_write_kernel(
     const int32_t *ids, uint64_t len, const uint32_t *tc, uint64_t ntiles,
-    const unsigned long long *boff, const int4 *minfo, pm_match *out, uint64_t cap)
+    const unsigned long long *boff, const int4 *minfo, pm_match *out, uint64_t cap,
+    uint64_t pos_base)
 {
     __shared__ unsigned long long toff[kTilesPerBlock];
     __shared__ uint32_t tcs[kTilesPerBlock];
@@ -145,7 +146,7 @@ __global__ void __launch_bounds__(1024, 1) pm_matches_write_kernel(
             for (int32_t k = 0; k < cnt; ++k) {
                 if (slot < cap) {
                     pm_match e;
-                    e.pos = q0 + r;
+                    e.pos = pos_base + q0 + r;
                     e.id = q;
                     e.len = mi.y;
                     out[slot] = e;
@@ -170,7 +171,8 @@ uint64_t match_work_bytes(uint64_t len)
 }
 
 int launch_matches(const TrieDev &t, const int32_t *ids, uint64_t len, void *work,
-                   pm_match *out, uint64_t capacity, void *stream, std::string &msg)
+                   pm_match *out, uint64_t capacity, void *stream, std::string &msg,
+                   uint64_t pos_base)
 {
     if (len == 0) return PM_OK;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
@@ -184,7 +186,7 @@ int launch_matches(const TrieDev &t, const int32_t *ids, uint64_t len, void *wor
     pm_tile_sums_kernel<<<(unsigned)nb, 1024, 0, st>>>(tc, ntiles, bsum);
     pm_block_scan_kernel<<<1, 1024, 0, st>>>(bsum, (uint32_t)nb, boff);
     pm_matches_write_kernel<<<(unsigned)nb, 1024, 0, st>>>(ids, len, tc, ntiles, boff, t.minfo,
-                                                           out, capacity);
+                                                           out, capacity, pos_base);
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) {
         msg = std::string("all-matches launch: ") + cudaGetErrorString(e);

@@ -140,7 +140,7 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *bar)
 
 // One try_wait: the thread is suspended until the phase completes or the
 // hinted time (ns) passes, so a waiting warp takes no issue slots.
-__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t phase)
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t phase, uint32_t hint_ns)
 {
     uint32_t done;
     asm volatile(
@@ -148,16 +148,39 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t phase)
         "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
         "selp.u32 %0, 1, 0, p;\n\t}"
         : "=r"(done)
-        : "r"(smem_u32(bar)), "r"(phase), "r"(kSuspendHintNs)
+        : "r"(smem_u32(bar)), "r"(phase), "r"(hint_ns)
+        : "memory");
+    return done != 0;
+}
+
+// Non-blocking test of the phase.
+__device__ __forceinline__ bool mbar_test_wait(uint64_t *bar, uint32_t phase)
+{
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(smem_u32(bar)), "r"(phase)
         : "memory");
     return done != 0;
 }
 
 // Bounded wait: false if the phase did not complete within `budget` clocks.
+// Budgets of a few milliseconds or more wait in suspending try_waits (1 ms
+// hint each); shorter ones poll with test_wait, since a suspended thread may
+// only wake when the phase completes.
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t phase, long long budget)
 {
     const long long t0 = clock64();
-    while (!mbar_try_wait(bar, phase)) {
+    if (budget < 8ll * kSuspendHintNs) {
+        while (!mbar_test_wait(bar, phase)) {
+            if (clock64() - t0 > budget) return false;
+        }
+        return true;
+    }
+    while (!mbar_try_wait(bar, phase, kSuspendHintNs)) {
         if (clock64() - t0 > budget) return false;
     }
     return true;
@@ -319,17 +342,14 @@ __device__ __forceinline__ uint32_t rel_end_of(unsigned long long e, unsigned lo
     return r > 0xFFFFFFFFull ? 0xFFFFFFFFu : (uint32_t)r;
 }
 
-// A walk from position pos ended at node v after matching `depth` bytes;
-// has: v's has-match bit (2: not read). Writes the position's id and adds
-// its count when a pattern ends on the path.
+// A walk from position pos ended at a node whose emit is {best, nfinal}
+// after matching `depth` bytes: writes the position's id and adds its count
+// when a pattern ends on the path.
 template <bool BATCH>
-__device__ __forceinline__ void emit_walk(const KParams &p, unsigned long long pos, uint32_t txt,
-                                          uint32_t v, uint32_t depth, uint32_t has,
-                                          unsigned long long &acc)
+__device__ __forceinline__ void emit_values(const KParams &p, unsigned long long pos, uint32_t txt,
+                                            uint32_t depth, int2 em, unsigned long long &acc)
 {
-    if (depth < p.t.min_len || has == 0u) return;
-    const int2 em = __ldg(p.t.emit + v);
-    if (!em.y) return;
+    if (depth < p.t.min_len || em.y <= 0) return;
     if (BATCH && p.out_ids)
         p.out_ids[txt][pos - __ldg(p.offsets + txt)] = em.x;
     else
@@ -340,6 +360,48 @@ __device__ __forceinline__ void emit_walk(const KParams &p, unsigned long long p
         acc += (unsigned)em.y;
         if (p.tile_counts) atomicAdd(p.tile_counts + (pos >> kMatchTileShift), (unsigned)em.y);
     }
+}
+
+// A walk from position pos ended at node v after matching `depth` bytes;
+// has: v's has-match bit (2: not read).
+template <bool BATCH>
+__device__ __forceinline__ void emit_walk(const KParams &p, unsigned long long pos, uint32_t txt,
+                                          uint32_t v, uint32_t depth, uint32_t has,
+                                          unsigned long long &acc)
+{
+    if (depth < p.t.min_len || has == 0u) return;
+    emit_values<BATCH>(p, pos, txt, depth, __ldg(p.t.emit + v), acc);
+}
+
+// Number of leading bytes on which a[0 .. n) and lab[0 .. n) agree, 16
+// bytes at a time: both are read as aligned 32-bit words, a text word only
+// when it holds a byte below a + n (lab is padded past its end).
+__device__ __forceinline__ uint32_t chain_match(const uint8_t *a, uint32_t n, const uint8_t *lab,
+                                                uint64_t pol)
+{
+    const uintptr_t aend = (uintptr_t)(a + n);
+    uint32_t m = 0;
+    while (m < n) {
+        const uintptr_t ta = (uintptr_t)(a + m), la = (uintptr_t)(lab + m);
+        const uint32_t *tw = reinterpret_cast<const uint32_t *>(ta & ~(uintptr_t)3);
+        const uint32_t *lw = reinterpret_cast<const uint32_t *>(la & ~(uintptr_t)3);
+        const uint32_t ts = (uint32_t)(ta & 3u) * 8u, ls = (uint32_t)(la & 3u) * 8u;
+        uint32_t x[5], y[5];
+#pragma unroll
+        for (int k = 0; k < 5; ++k) {
+            x[k] = (uintptr_t)(tw + k) < aend ? __ldg(tw + k) : 0u;
+            y[k] = ld_trie_u32(lw + k, pol);
+        }
+        uint32_t d = 16;
+#pragma unroll
+        for (int k = 3; k >= 0; --k) {
+            const uint32_t z = __funnelshift_r(x[k], x[k + 1], ts) ^ __funnelshift_r(y[k], y[k + 1], ls);
+            if (z) d = 4u * k + ((uint32_t)(__ffs(z) - 1) >> 3);
+        }
+        m += d;
+        if (d < 16) break;
+    }
+    return m < n ? m : n;
 }
 
 // The node at which a rank table (uint2 {bits, base} per 32 codes) places
@@ -434,6 +496,25 @@ __device__ __forceinline__ void run_walk(const KParams &p, unsigned long long qp
         }
         if (MODE == MODE_LOOKUPS) ++look;
         if (deg == 0) break;  // leaf
+        if (MODE != MODE_LOOKUPS && deg == 1u && (r.z >> 8) >= 2u) {
+            // a unary chain: the next R edges are forced; compare the text
+            // with their labels in one go and land on the node reached
+            const uint32_t R = r.z >> 8, ci = r.w;
+            if (MODE == MODE_CHECKED && (ci >= t.ch_len || R > t.ch_len - 1u - ci)) {
+                record_error(PM_ERR_BOUNDS);
+                return;
+            }
+            const uint32_t m = chain_match(tp + jo, min(R, te - jo), t.ch_lab + ci, pol);
+            const int2 inf = __ldg(t.ch_info + ci + m);
+            jo += m;
+            if (m < R) {  // stopped inside the chain: mismatch or text end
+                emit_values<BATCH>(p, pos, txt, jo, inf, acc);
+                return;
+            }
+            v = (uint32_t)inf.x;  // the chain's end node
+            has = 2u;
+            continue;
+        }
         const uint32_t ei = row_find(t.col, r.x, deg, r.z, r.w, b, p.binary, pol);
         if (ei == 0xFFFFFFFFu) break;
         v = ei + 1u;  // BFS order: the child of non-zero e is node e + 1
@@ -446,11 +527,13 @@ __device__ __forceinline__ void run_walk(const KParams &p, unsigned long long qp
 // Classes of the P bytes at st[o .. o + P), packed msb-first (byte o's class
 // in the top cb bits of a P*cb-bit chunk), from the lane-replicated table
 // (word (b/4)*32 + lane holds the entries of bytes 4*(b/4) .. +3, so lane l
-// always reads bank l); *oth: some byte is of the "other" class.
+// always reads bank l); *oth (meaningful with other_check, where classes
+// take at most 7 bits): some byte is of the "other" class.
 template <int P>
 __device__ __forceinline__ uint32_t classify(const uint8_t *st, const uint32_t *s_lut,
                                              uint32_t lane, uint32_t cb, uint32_t &oth)
 {
+    const uint32_t cmask = (1u << cb) - 1u;
     uint32_t c = 0, o = 0;
 #pragma unroll
     for (int w = 0; w < P / 4; ++w) {
@@ -459,7 +542,7 @@ __device__ __forceinline__ uint32_t classify(const uint8_t *st, const uint32_t *
         for (int j = 0; j < 4; ++j) {
             const uint32_t b = (word >> (8 * j)) & 0xFFu;
             const uint32_t v = (s_lut[(b >> 2) * 32 + lane] >> ((b & 3u) * 8u)) & 0xFFu;
-            c = (c << cb) | (v & 0x7Fu);
+            c = (c << cb) | (v & cmask);
             o |= v;
         }
     }
@@ -470,9 +553,14 @@ __device__ __forceinline__ uint32_t classify(const uint8_t *st, const uint32_t *
 // KF: the byte alphabet's filter level k (0, 1, 2), or -1 for byte classes.
 // G: bytes the byte alphabet's Bloom filter tests (3 or 4), 0 otherwise.
 // P: start positions per lane and group.
-template <int KF, int G, bool IDENT, bool BATCH, int MODE, int P>
+// CB, FC, DC (byte classes): bits per class, filter depth and deep-level
+// depth fixed at compile time (all shifts of the packed codes become
+// constants), or 0 when taken from the parameters at run time.
+template <int KF, int G, bool IDENT, bool BATCH, int MODE, int P, int CB = 0, int FC = 0, int DC = 0>
 __global__ void __launch_bounds__(1024, 1) pfac_scan_kernel(const KParams p)
 {
+    constexpr bool FIXED = CB > 0 && FC > 0 && DC > 0;
+    constexpr uint32_t NNBC = FIXED ? ((FC > DC ? FC : DC) - 1 + P - 1) / P : 0;
     extern __shared__ __align__(16) uint8_t smem[];
     const TrieDev &t = p.t;
     const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -546,8 +634,10 @@ __global__ void __launch_bounds__(1024, 1) pfac_scan_kernel(const KParams p)
         constexpr uint32_t KFU = KF > 0 ? (uint32_t)KF : 0u;
         const uint32_t imask = KF >= 0 ? (uint32_t)((1ull << (8 * KFU + lw)) - 1ull) : 0u;
         // byte classes: bits of one lane's chunk, code shifts
-        const uint32_t cb = p.cb, Pcb = P * cb;
-        const uint32_t shF = 32u - cb * p.F, shD = 32u - cb * p.D;  // used only when F, D > 0
+        const uint32_t cb = CB ? (uint32_t)CB : p.cb, Pcb = P * cb;
+        const uint32_t Fv = FIXED ? (uint32_t)FC : p.F, Dv = FIXED ? (uint32_t)DC : p.D;
+        const uint32_t nnb = FIXED ? NNBC : p.nnb;
+        const uint32_t shF = 32u - cb * Fv, shD = 32u - cb * Dv;  // used only when F, D > 0
         const uint32_t span = (p.gram > 1 ? p.gram : 1u) - 1u;  // bytes a position's filter reads past it
         bool failed = false;
 
@@ -625,14 +715,14 @@ __global__ void __launch_bounds__(1024, 1) pfac_scan_kernel(const KParams p)
                     X = (uint64_t)cur_c << (64u - Pcb);
 #pragma unroll
                     for (int d = 1; d <= kMaxNeighbours; ++d) {
-                        if ((uint32_t)d > p.nnb) break;
+                        if ((uint32_t)d > nnb) break;
                         const uint32_t src = (lane + d) & 31u;
                         const uint32_t a = __shfl_sync(kFull, cur_c, src);
                         const uint32_t b = __shfl_sync(kFull, nxt_c, src);
                         X |= (uint64_t)(lane + d < 32 ? a : b) << (64u - (d + 1) * Pcb);
                     }
                     if (t.other_check &&
-                        __any_sync(kFull, cur_o != 0 || (lane < p.nnb && nxt_o != 0)))
+                        __any_sync(kFull, cur_o != 0 || (lane < nnb && nxt_o != 0)))
                         fast = false;  // a byte of no pattern: decide per position
                 }
                 if (fast) {
@@ -678,6 +768,48 @@ __global__ void __launch_bounds__(1024, 1) pfac_scan_kernel(const KParams p)
                         if (KF == 0) {  // no dense level: passing positions walk from the root
                             rootm = need;
                             need = 0;
+                        }
+                    } else if (FIXED) {
+                        // byte classes, shapes fixed at compile time: every
+                        // code is a constant shift of the window
+                        constexpr uint32_t FM = (1u << (CB * FC)) - 1u, DM = (1u << (CB * DC)) - 1u;
+#pragma unroll
+                        for (int q = 0; q < P; ++q) {
+                            const uint32_t code = (uint32_t)(X >> (64 - CB * (q + FC))) & FM;
+                            if (MODE == MODE_CHECKED && (code >> 5) >= p.filt_words) {
+                                record_error(PM_ERR_BOUNDS);
+                                continue;
+                            }
+                            need |= ((s_filt[code >> 5] >> (code & 31u)) & 1u) << q;
+                        }
+                        if (need) {
+#pragma unroll
+                            for (int q = 0; q < P; ++q)
+                                if (((need >> q) & 1u) && lp0 + q + DC > rel_end) {
+                                    need &= ~(1u << q);
+                                    rootm |= 1u << q;
+                                }
+                            if (DC > FC && need) {
+                                uint32_t dw[P];
+#pragma unroll
+                                for (int q = 0; q < P; ++q) {
+                                    dw[q] = 0;
+                                    if (!((need >> q) & 1u)) continue;
+                                    const uint32_t code = (uint32_t)(X >> (64 - CB * (q + DC))) & DM;
+                                    if (MODE == MODE_CHECKED && (code >> 5) >= t.deep_words) {
+                                        record_error(PM_ERR_BOUNDS);
+                                        need &= ~(1u << q);
+                                        continue;
+                                    }
+                                    dw[q] = ld_trie_u32(t.deep + (code >> 5), pol);
+                                }
+#pragma unroll
+                                for (int q = 0; q < P; ++q) {
+                                    const uint32_t code = (uint32_t)(X >> (64 - CB * (q + DC))) & DM;
+                                    if (((need >> q) & 1u) && !((dw[q] >> (code & 31u)) & 1u))
+                                        need &= ~(1u << q);
+                                }
+                            }
                         }
                     } else {
                         // byte classes: the F-gram at each position in the
@@ -778,10 +910,10 @@ __global__ void __launch_bounds__(1024, 1) pfac_scan_kernel(const KParams p)
                             for (uint32_t j = 0; j < p.F; ++j) {
                                 const uint32_t b = st[lp + j];
                                 const uint32_t v = (s_lut[(b >> 2) * 32 + lane] >> ((b & 3u) * 8u)) & 0xFFu;
-                                code = (code << cb) | (v & 0x7Fu);
+                                code = (code << cb) | (v & ((1u << cb) - 1u));
                                 oth |= v & 0x80u;
                             }
-                            if (oth) continue;  // a byte of no pattern: no match here
+                            if (t.other_check && oth) continue;  // a byte of no pattern: no match here
                             word = code >> 5;
                             bits = 1u << (code & 31u);
                         }
@@ -805,6 +937,14 @@ __global__ void __launch_bounds__(1024, 1) pfac_scan_kernel(const KParams p)
                         }
                         __stcs(p.out_ids[c2] + (pos - __ldg(p.offsets + c2)), -1);
                     }
+                } else if (p.ids_aligned && i * GP + GP <= tile_n) {
+                    // every id of the group is -1: the warp writes the
+                    // group's 32P ids as P/4 fully coalesced 512-byte rows,
+                    // whichever lane owns the positions
+#pragma unroll
+                    for (int j = 0; j < P / 4; ++j)
+                        __stcs(reinterpret_cast<int4 *>(idt + i * GP) + 32 * j + lane,
+                               make_int4(-1, -1, -1, -1));
                 } else if (p.ids_aligned && lp0 + P <= tile_n) {
 #pragma unroll
                     for (int j = 0; j < P / 4; ++j)
@@ -851,6 +991,7 @@ __global__ void __launch_bounds__(1024, 1) pfac_scan_kernel(const KParams p)
                         return pos | ((unsigned long long)WALK_DEEP << 61);
                     };
                     if (tot > kQueue) {
+                        __syncwarp();  // the group's -1 stores (any lane's) first
                         uint32_t wk = work;
                         while (wk) {
                             const uint32_t q = __ffs(wk) - 1;
@@ -911,42 +1052,159 @@ __global__ void __launch_bounds__(1024, 1) pfac_scan_kernel(const KParams p)
 
 typedef void (*KernelFn)(KParams);
 
-template <int KF, int G, bool IDENT, int P>
+template <int KF, int G, bool IDENT, int P, int CB = 0, int FC = 0, int DC = 0>
 KernelFn pick_mode(bool batch, int mode)
 {
     if (batch) {
         switch (mode) {
-        case MODE_CHECKED: return pfac_scan_kernel<KF, G, IDENT, true, MODE_CHECKED, P>;
+        case MODE_CHECKED: return pfac_scan_kernel<KF, G, IDENT, true, MODE_CHECKED, P, CB, FC, DC>;
         case MODE_LOOKUPS: return pfac_scan_kernel<KF, G, IDENT, true, MODE_LOOKUPS, 4>;
-        default: return pfac_scan_kernel<KF, G, IDENT, true, MODE_FAST, P>;
+        default: return pfac_scan_kernel<KF, G, IDENT, true, MODE_FAST, P, CB, FC, DC>;
         }
     }
     switch (mode) {
-    case MODE_CHECKED: return pfac_scan_kernel<KF, G, IDENT, false, MODE_CHECKED, P>;
+    case MODE_CHECKED: return pfac_scan_kernel<KF, G, IDENT, false, MODE_CHECKED, P, CB, FC, DC>;
     case MODE_LOOKUPS: return pfac_scan_kernel<KF, G, IDENT, false, MODE_LOOKUPS, 4>;
-    default: return pfac_scan_kernel<KF, G, IDENT, false, MODE_FAST, P>;
+    default: return pfac_scan_kernel<KF, G, IDENT, false, MODE_FAST, P, CB, FC, DC>;
     }
 }
 
 template <int P>
-KernelFn pick_kernel_p(uint32_t C, uint32_t k, uint32_t gram, bool batch, int mode)
+KernelFn pick_kernel_p(const TrieDev &t, uint32_t k, uint32_t gram, uint32_t D, bool batch,
+                       int mode)
 {
-    if (C == 256) {
+    if (t.C == 256) {
         if (k == 0) return pick_mode<0, 0, true, P>(batch, mode);
         if (k == 1) return pick_mode<1, 0, true, P>(batch, mode);
         if (gram == 4) return pick_mode<2, 4, true, P>(batch, mode);
         return pick_mode<2, 3, true, P>(batch, mode);
     }
+    // four-letter alphabets (two bits a class) with every pattern at least
+    // 13 long, e.g. DNA: the deepest filter and deep level, fixed
+    if (t.cb == 2 && k == 10 && D == 13) return pick_mode<-1, 0, false, P, 2, 10, 13>(batch, mode);
     return pick_mode<-1, 0, false, P>(batch, mode);
 }
 
 // Byte alphabet (C = 256): k is 0, 1 or 2 and fixed at compile time, and so
 // is the Bloom gram length at k = 2. The instrumented lookup-counting kernel
 // always takes four positions per lane.
-KernelFn pick_kernel(uint32_t C, uint32_t k, uint32_t gram, bool batch, int mode, int positions)
+KernelFn pick_kernel(const TrieDev &t, uint32_t k, uint32_t gram, uint32_t D, bool batch,
+                     int mode, int positions)
 {
-    if (positions == 8 && mode != MODE_LOOKUPS) return pick_kernel_p<8>(C, k, gram, batch, mode);
-    return pick_kernel_p<4>(C, k, gram, batch, mode);
+    if (positions == 8 && mode != MODE_LOOKUPS)
+        return pick_kernel_p<8>(t, k, gram, D, batch, mode);
+    return pick_kernel_p<4>(t, k, gram, D, batch, mode);
+}
+
+// Light form for short single texts: no shared-memory tables, no staging,
+// small CTAs, four positions per thread. Each position reads its bytes
+// through L1, tests the filter word in global memory (L2-resident), writes
+// -1, and walks at once when the filter cannot rule it out; the same
+// filters, start nodes and walks as the persistent kernel, so the same bits.
+// Launching it costs a few microseconds where the persistent kernel loads
+// up to 128 KiB of tables into every CTA first.
+template <int KF, int G, bool IDENT, int MODE>
+__global__ void __launch_bounds__(256) pfac_light_kernel(const KParams p)
+{
+    constexpr int P = 4;
+    const TrieDev &t = p.t;
+    const uint64_t pol = policy_evict_last();
+    const uint32_t lane = threadIdx.x & 31;
+    unsigned long long acc = 0, look = 0, nwalk = 0;
+    const unsigned long long i0 = ((unsigned long long)blockIdx.x * blockDim.x + threadIdx.x) * P;
+    constexpr uint32_t KFU = KF > 0 ? (uint32_t)KF : 0u;
+    const uint32_t cb = p.cb;
+    for (int q = 0; q < P; ++q) {
+        const unsigned long long pos = i0 + q;
+        if (pos >= p.total) break;
+        __stcs(p.ids + pos, -1);
+        const unsigned long long left = p.limit - pos;  // readable bytes from pos
+        const uint8_t *tp = p.text + pos;
+        unsigned long long e = pos;  // root walk unless the filter says otherwise
+        uint32_t code = 0;
+        bool walk = true;
+        if (MODE != MODE_LOOKUPS && p.gram <= left) {
+            if (IDENT) {
+                uint32_t x = 0;
+                for (uint32_t j = 0; j < p.gram; ++j) x |= (uint32_t)__ldg(tp + j) << (8 * j);
+                uint32_t word, bits;
+                if (KF >= (int)kBloomK) {
+                    const BloomProbe b = bloom_probe(x, p.gram, 8u * KFU + p.lw - 5u);
+                    word = b.word;
+                    bits = b.mask;
+                } else {
+                    const uint32_t idx = x & (uint32_t)((1ull << (8 * KFU + p.lw)) - 1ull);
+                    word = idx >> 5;
+                    bits = 1u << (idx & 31u);
+                }
+                if (MODE == MODE_CHECKED && word >= p.filt_words) {
+                    record_error(PM_ERR_BOUNDS);
+                    continue;
+                }
+                walk = (ld_trie_u32(p.filter + word, pol) & bits) == bits;
+                if (walk && KF >= 1) {
+                    code = KF == 1 ? (x & 0xFFu) : ((x & 0xFFu) << 8) | ((x >> 8) & 0xFFu);
+                    e = pos | ((unsigned long long)WALK_DENSE << 61);
+                }
+            } else if (p.F > 0) {
+                uint32_t c = 0, oth = 0;
+                for (uint32_t j = 0; j < p.F; ++j) {
+                    const uint32_t v = __ldg(t.cls + __ldg(tp + j));
+                    c = (c << cb) | (v & ((1u << cb) - 1u));
+                    oth |= v & 0x80u;
+                }
+                if (t.other_check && oth) continue;  // a byte of no pattern: no match
+                if (MODE == MODE_CHECKED && (c >> 5) >= p.filt_words) {
+                    record_error(PM_ERR_BOUNDS);
+                    continue;
+                }
+                walk = (ld_trie_u32(p.filter + (c >> 5), pol) >> (c & 31u)) & 1u;
+                if (walk && p.D > 0 && p.D <= left) {
+                    for (uint32_t j = p.F; j < p.D; ++j) {
+                        const uint32_t v = __ldg(t.cls + __ldg(tp + j));
+                        c = (c << cb) | (v & ((1u << cb) - 1u));
+                        oth |= v & 0x80u;
+                    }
+                    if (t.other_check && oth) continue;
+                    code = c;
+                    e = pos | ((unsigned long long)WALK_DEEP << 61);
+                }
+            }
+        }
+        if (walk) run_walk<false, MODE>(p, e, code, p.limit, pol, acc, look, nwalk);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        acc += __shfl_xor_sync(kFull, acc, o);
+        look += __shfl_xor_sync(kFull, look, o);
+        nwalk += __shfl_xor_sync(kFull, nwalk, o);
+    }
+    if (lane == 0) {
+        if (acc) atomicAdd(reinterpret_cast<unsigned long long *>(p.counts), acc);
+        if (MODE == MODE_LOOKUPS && look && p.lookups) atomicAdd(p.lookups, look);
+        if (p.walks && nwalk) atomicAdd(p.walks, nwalk);
+    }
+}
+
+template <int KF, int G, bool IDENT>
+KernelFn pick_light_mode(int mode)
+{
+    switch (mode) {
+    case MODE_CHECKED: return pfac_light_kernel<KF, G, IDENT, MODE_CHECKED>;
+    case MODE_LOOKUPS: return pfac_light_kernel<KF, G, IDENT, MODE_LOOKUPS>;
+    default: return pfac_light_kernel<KF, G, IDENT, MODE_FAST>;
+    }
+}
+
+KernelFn pick_light(const TrieDev &t, uint32_t k, uint32_t gram, int mode)
+{
+    if (t.C == 256) {
+        if (k == 0) return pick_light_mode<0, 0, true>(mode);
+        if (k == 1) return pick_light_mode<1, 0, true>(mode);
+        if (gram == 4) return pick_light_mode<2, 4, true>(mode);
+        return pick_light_mode<2, 3, true>(mode);
+    }
+    return pick_light_mode<-1, 0, false>(mode);
 }
 
 // Per-text count finalisation: counts[t] to the caller's *out[t].
@@ -1043,8 +1301,9 @@ int launch_scan(const TrieDev &t, const pm_config &cfg, const ScanArgs &a, void 
     pm_config c = cfg;
     if (mode == MODE_LOOKUPS) c.positions = 4;
     const bool ident = t.C == 256;
-    KernelFn fn = pick_kernel(t.C, (uint32_t)c.dense_k, ident ? t.gram[c.dense_k] : 0u, batch,
-                              mode, c.positions);
+    const uint32_t deep_d = !ident && c.deep && t.deep_k > 0 ? t.deep_k : 0u;
+    KernelFn fn = pick_kernel(t, (uint32_t)c.dense_k, ident ? t.gram[c.dense_k] : 0u, deep_d,
+                              batch, mode, c.positions);
     const ScanLayout L = scan_layout(t, c);
 
     KParams p{};
@@ -1093,6 +1352,19 @@ int launch_scan(const TrieDev &t, const pm_config &cfg, const ScanArgs &a, void 
     p.filt_words = L.filt_words;
 
     cudaError_t e;
+    if (!batch && c.light_max > 0 && a.len <= (uint64_t)c.light_max) {
+        const uint32_t threads = 128;
+        const unsigned long long per = 4ull * threads;
+        const unsigned long long grid = (a.len + per - 1) / per;
+        KernelFn lf = pick_light(t, (uint32_t)c.dense_k, ident ? t.gram[c.dense_k] : 0u, mode);
+        lf<<<(unsigned)grid, threads, 0, st>>>(p);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) {
+            msg = std::string("light scan launch: ") + cudaGetErrorString(e);
+            return PM_ERR_CUDA;
+        }
+        return PM_OK;
+    }
     int occ = 0;
     {
         // the shared-memory attribute and the occupancy of each (kernel,

@@ -35,7 +35,8 @@ EXPORTS = (
     "pm_scan_host", "pm_scan_host_static", "pm_device_error", "pm_strerror", "pm_last_error",
     "pm_last_error_msg", "pm_server_create", "pm_submit", "pm_poll", "pm_wait",
     "pm_server_get_stats", "pm_server_destroy", "pm_server_replay", "pm_replay_plain",
-    "pm_scan_all", "pm_scan_all_work_bytes", "pm_scan_walks",
+    "pm_scan_all", "pm_scan_all_work_bytes", "pm_scan_walks", "pm_scan_range",
+    "pm_scan_all_host",
     "pm_scanner_open", "pm_scanner_push", "pm_scanner_finish", "pm_scanner_close",
 )
 
@@ -85,7 +86,7 @@ class pm_config(C.Structure):
     _fields_ = [(f, C.c_int32) for f in (
         "threads", "tile", "dense_k", "filter_bits", "row_search",
         "ctas_per_sm", "stages", "checked", "positions", "deep", "layout",
-        "wait_clocks")]
+        "wait_clocks", "light_max")]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -139,6 +140,8 @@ def load(path: Optional[str] = None):
         "pm_scan_all": ([P, P, u64, pm_result, P, u64, P, u64, P], C.c_int),
         "pm_scan_all_work_bytes": ([u64], u64),
         "pm_scan_walks": ([P, P, u64, P, P, P, P, P], C.c_int),
+        "pm_scan_range": ([P, P, u64, u64, u64, pm_result, P], C.c_int),
+        "pm_scan_all_host": ([P, P, u64, P, u64, P], C.c_int),
         "pm_scanner_open": ([P, P], C.c_int),
         "pm_scanner_push": ([P, P, u64, P, P, P, P], C.c_int),
         "pm_scanner_finish": ([P, P, P, P, P], C.c_int),
@@ -279,6 +282,19 @@ def pm_scan(trie: Trie, text, ids, count, stream=None, length: Optional[int] = N
                           _stream_ptr(stream)), "pm_scan")
 
 
+def pm_scan_range(trie: Trie, text, start: int, end: int, limit: int, ids, count,
+                  stream=None):
+    """Scan start positions [start, end) of a device text (uint8 tensor of at
+    least `limit` bytes) whose walks may read up to `limit`; ids
+    (int32[end - start]) and count (int64[1])."""
+    import torch
+    if limit > text.numel():
+        raise PMError(PM_ERR_INVAL, "pm_scan_range", "limit beyond the text tensor")
+    out = pm_result(_dptr(ids, torch.int32, "ids"), _dptr(count, torch.int64, "count"))
+    _check(load().pm_scan_range(trie.handle, _dptr(text, torch.uint8, "text"), start, end,
+                                limit, out, _stream_ptr(stream)), "pm_scan_range")
+
+
 def pm_scan_walks(trie: Trie, text, ids, count, walks, cfg: Optional[dict] = None,
                   stream=None, length: Optional[int] = None):
     """pm_scan that also counts the walks queued into `walks` (int64[1])."""
@@ -316,10 +332,29 @@ def pm_scan_all(trie: Trie, text, ids, count, matches, work, stream=None,
                               _stream_ptr(stream)), "pm_scan_all")
 
 
+def pm_scan_all_host(trie: Trie, text: np.ndarray, matches: np.ndarray) -> int:
+    """Every occurrence in a host text (uint8 numpy, ideally pinned), listed
+    into `matches` (a C-contiguous int64 numpy array of shape [capacity, 2]
+    holding pm_match records, see decode_matches); returns the total count
+    (the list stops after `capacity` records)."""
+    if text.dtype != np.uint8 or not text.flags.c_contiguous:
+        raise PMError(PM_ERR_INVAL, "pm_scan_all_host", "text must be C-contiguous uint8")
+    if matches.dtype != np.int64 or matches.ndim != 2 or matches.shape[1] != 2 or \
+            not matches.flags.c_contiguous or not matches.flags.writeable:
+        raise PMError(PM_ERR_INVAL, "pm_scan_all_host",
+                      "matches must be a writeable C-contiguous int64 array [capacity, 2]")
+    cnt = C.c_uint64()
+    _check(load().pm_scan_all_host(trie.handle, text.ctypes.data if text.size else None,
+                                   text.size, matches.ctypes.data if matches.size else None,
+                                   matches.shape[0], C.byref(cnt)), "pm_scan_all_host")
+    return cnt.value
+
+
 def decode_matches(matches, m: int):
     """(pos int64[m], id int32[m], length int32[m]) from the first m pm_match
     records of an int64 [capacity, 2] tensor."""
-    a = matches[:m].cpu().numpy()
+    a = matches[:m]
+    a = a.cpu().numpy() if hasattr(a, "cpu") else np.asarray(a)
     hi = a[:, 1].view(np.uint64)
     return (a[:, 0].copy(), (hi & 0xFFFFFFFF).astype(np.uint32).view(np.int32),
             (hi >> 32).astype(np.uint32).view(np.int32))

@@ -20,8 +20,9 @@ from typing import Dict, Iterable, List, Optional
 from . import pm
 
 
-def candidates(trie: pm.Trie, total_bytes: int) -> List[dict]:
-    """Valid configurations to time for an input of `total_bytes` bytes."""
+def candidates(trie: pm.Trie, total_bytes: int, single: bool = False) -> List[dict]:
+    """Valid configurations to time for an input of `total_bytes` bytes (a
+    single text when `single`: short ones may also take the light form)."""
     st = pm.pm_stats(trie)
     base = pm.pm_get_config(trie)
     kmax = st["dense_k_max"]
@@ -31,12 +32,13 @@ def candidates(trie: pm.Trie, total_bytes: int) -> List[dict]:
     # small inputs cannot fill large CTAs: smaller ones launch and start faster
     threads = [base["threads"], 512] + ([256, 128] if total_bytes <= (4 << 20) else [])
     tiles = (256, 1024, 2048) if total_bytes <= (4 << 20) else (1024, 2048, 4096)
+    lights = (0, 1 << 30) if single and total_bytes <= (1 << 20) else (0,)
     out, seen = [], set()
-    for th, tile, stages, k, bits, pos, rs in itertools.product(
-            threads, tiles, (2, 3), ks, widths, (4, 8), (0, 1)):
+    for th, tile, stages, k, bits, pos, rs, lm in itertools.product(
+            threads, tiles, (2, 3), ks, widths, (4, 8), (0, 1), lights):
         c = dict(base, threads=th, tile=tile, stages=stages, dense_k=k, filter_bits=bits,
                  positions=pos, row_search=rs, checked=0, ctas_per_sm=0, layout=0,
-                 wait_clocks=0, deep=0 if ident else (1 if st["deep_k"] else 0))
+                 wait_clocks=0, light_max=lm, deep=0 if ident else (1 if st["deep_k"] else 0))
         key = tuple(sorted(c.items()))
         if key in seen:
             continue
@@ -99,7 +101,7 @@ def autotune(trie: pm.Trie, texts, offsets=None, ids=None, counts=None,
                              device=texts.device)
     best = None
     tried = 0
-    for c in (list(cands) if cands is not None else candidates(trie, total)):
+    for c in (list(cands) if cands is not None else candidates(trie, total, single=not batch)):
         def run(c=c):
             pm.pm_scan_ex(trie, texts, offsets, ids, counts, cfg=c)
         try:

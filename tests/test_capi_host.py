@@ -171,7 +171,8 @@ def test_config_validation(lib):
     pm.pm_set_config(t, cfg)
     for bad in ({"threads": 100}, {"threads": 1056}, {"tile": 1000}, {"dense_k": -1},
                 {"stages": 9}, {"dense_k": 99}, {"filter_bits": 16}, {"deep": 2},
-                {"positions": 5}, {"positions": 8, "tile": 128}, {"wait_clocks": -1}):
+                {"positions": 5}, {"positions": 8, "tile": 128}, {"wait_clocks": -1},
+                {"light_max": -1}):
         c = dict(cfg, **bad)
         with pytest.raises(pm.PMError) as e:
             pm.pm_set_config(t, c)
@@ -201,6 +202,30 @@ def test_scan_all_host_side(lib):
     res = pm.pm_result(None, C.addressof(cnt))
     assert lib.pm_scan_all(t.handle, None, 0, res, None, 0, None, 0, None) == pm.PM_ERR_HOST_ONLY
     assert lib.pm_scan_all(t.handle, None, 5, res, None, 0, None, 0, None) == pm.PM_ERR_INVAL
+
+
+def test_scan_all_host_errors(lib):
+    import ctypes as C
+    t = pm.pm_build_host([b"abc"])
+    cnt = C.c_uint64()
+    assert lib.pm_scan_all_host(None, None, 0, None, 0, C.byref(cnt)) == pm.PM_ERR_INVAL
+    assert lib.pm_scan_all_host(t.handle, None, 0, None, 0, C.byref(cnt)) == pm.PM_ERR_HOST_ONLY
+    with pytest.raises(pm.PMError):
+        pm.pm_scan_all_host(t, np.zeros(8, np.uint8)[::2], np.zeros((4, 2), np.int64))
+    with pytest.raises(pm.PMError):
+        pm.pm_scan_all_host(t, np.zeros(8, np.uint8), np.zeros((4, 3), np.int64))
+
+
+def test_scan_range_host_side(lib):
+    import ctypes as C
+    t = pm.pm_build_host([b"abc"])
+    cnt = C.c_int64()
+    res = pm.pm_result(None, C.addressof(cnt))
+    assert lib.pm_scan_range(t.handle, None, 5, 3, 10, res, None) == pm.PM_ERR_INVAL
+    assert lib.pm_scan_range(t.handle, None, 0, 10, 5, res, None) == pm.PM_ERR_INVAL
+    assert lib.pm_scan_range(t.handle, None, 0, 4, 4, res, None) == pm.PM_ERR_INVAL
+    assert lib.pm_scan_range(t.handle, None, 3, 3, 3, res, None) == pm.PM_ERR_HOST_ONLY
+    assert lib.pm_scan_range(None, None, 3, 3, 3, res, None) == pm.PM_ERR_INVAL
 
 
 def test_scanner_host_side(lib):

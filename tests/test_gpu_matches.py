@@ -146,3 +146,43 @@ def test_paper_scale_full_size_all():
         e = ot.scan_all(wl.text, a, b)
         sel = (got[0] >= a) & (got[0] < b)
         assert_all_same(tuple(g[sel] for g in got), e)
+
+
+def test_scan_all_host_chunks_and_capacity():
+    """pm_scan_all_host: a host text longer than one 32 MiB chunk, with
+    occurrences straddling the chunk boundary, listed in host memory exactly
+    as the oracle lists them (positions are the whole text's); a capacity
+    below the count keeps the list's first entries and reports the total;
+    a list that outgrows the initial device buffers (dense ACGT) too."""
+    pats = W.paper_scale(0, text_bytes=16, n_patterns=2000).patterns
+    rng = np.random.Generator(np.random.MT19937(9))
+    n = 40 * W.MiB + 77
+    text = rng.integers(0, 256, size=n, dtype=np.uint8)
+    W._plant_bernoulli(rng, text, pats, 1.0 / 4096)
+    p = np.frombuffer(pats.get(int(np.argmax(pats.lengths()))), np.uint8)
+    cut = 32 * W.MiB
+    text[cut - len(p) // 2: cut - len(p) // 2 + len(p)] = p
+    t = pm.pm_build(pats)
+    h_text = torch.from_numpy(text).pin_memory().numpy()
+    ot = oracle.Trie(pats)
+    e_pos, e_id, e_len = ot.scan_all(text, threads=8)
+    assert len(e_pos) > 5000 and np.any((e_pos < cut) & (e_pos + e_len > cut))
+    m = np.full((len(e_pos) + 10, 2), -9, dtype=np.int64)
+    total = pm.pm_scan_all_host(t, h_text, m)
+    assert total == len(e_pos)
+    g_pos, g_id, g_len = pm.decode_matches(m, total)
+    assert np.array_equal(g_pos, e_pos) and np.array_equal(g_id, e_id) and np.array_equal(g_len, e_len)
+    small = np.full((100, 2), -9, dtype=np.int64)
+    assert pm.pm_scan_all_host(t, h_text, small) == len(e_pos)
+    s_pos, s_id, s_len = pm.decode_matches(small, 100)
+    assert np.array_equal(s_pos, e_pos[:100]) and np.array_equal(s_id, e_id[:100])
+    # dense listing: more occurrences per chunk than the initial list buffers
+    wl = W.acgt(3, text_bytes=12 * W.MiB + 5, n_patterns=20000, plant_rate=0.02)
+    ta = pm.pm_build(wl.patterns)
+    a_pos, a_id, a_len = oracle.Trie(wl.patterns).scan_all(wl.text, threads=8)
+    assert len(a_pos) > (1 << 17)
+    ma = np.zeros((len(a_pos), 2), dtype=np.int64)
+    assert pm.pm_scan_all_host(ta, wl.text, ma) == len(a_pos)
+    g_pos, g_id, g_len = pm.decode_matches(ma, len(a_pos))
+    assert np.array_equal(g_pos, a_pos) and np.array_equal(g_id, a_id) and np.array_equal(g_len, a_len)
+    assert pm.pm_scan_all_host(ta, wl.text[:0], ma) == 0

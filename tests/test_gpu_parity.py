@@ -69,10 +69,21 @@ def assert_same(ids, cnt, o_ids, o_cnt):
 
 
 def small_cfg(trie, **kw):
+    """A small persistent-kernel configuration (the light form off)."""
     c = pm.pm_get_config(trie)
-    c.update(threads=128, tile=256, stages=2, positions=4)
+    c.update(threads=128, tile=256, stages=2, positions=4, light_max=0)
     c.update(kw)
     return c
+
+
+def persistent(trie, **kw):
+    """The handle's configuration with the light form off."""
+    return dict(pm.pm_get_config(trie), light_max=0, **kw)
+
+
+def light(trie, **kw):
+    """The handle's configuration with the light form for every length."""
+    return dict(pm.pm_get_config(trie), light_max=1 << 30, **kw)
 
 
 # --------------------------------------------------------------------------
@@ -90,8 +101,9 @@ def test_golden_fixtures():
         assert ids.tolist() == c["ids"], f
         assert cnt == c["count"], f
         assert look == c["lookups"], f
-        ids2, cnt2, _ = gpu_scan(t, text)
-        assert ids2.tolist() == c["ids"] and cnt2 == c["count"], f
+        for cfg in (None, persistent(t), light(t)):
+            ids2, cnt2, _ = gpu_scan(t, text, cfg=cfg)
+            assert ids2.tolist() == c["ids"] and cnt2 == c["count"], f
 
 
 @pytest.mark.parametrize("seed,alphabet,npat,lo,hi,n", [
@@ -124,7 +136,7 @@ def test_config_sweep():
                     for bits in (8, 16, 32):
                         for rs in (0, 1):
                             c = dict(base, threads=threads, tile=tile, dense_k=k,
-                                     filter_bits=bits, row_search=rs,
+                                     filter_bits=bits, row_search=rs, light_max=0,
                                      stages=2 + (tile == 128) * 2,
                                      checked=int(threads == 256),
                                      positions=(4, 8)[(rs + threads // 128) % 2])
@@ -144,8 +156,9 @@ def test_unaligned_and_ragged():
     t = pm.pm_build(wl.patterns)
     o_ids, o_cnt, _ = oracle.Trie(wl.patterns).scan(wl.text)
     for off in (1, 3, 8, 15):
-        ids, cnt, _ = gpu_scan(t, wl.text, offset=off)
-        assert_same(ids, cnt, o_ids, o_cnt)
+        for cfg in (persistent(t), light(t)):
+            ids, cnt, _ = gpu_scan(t, wl.text, cfg=cfg, offset=off)
+            assert_same(ids, cnt, o_ids, o_cnt)
     # ids pointer not 16-byte aligned
     tv = dev(wl.text)
     big = torch.zeros(len(wl.text) + 1, dtype=torch.int32, device="cuda")
@@ -186,6 +199,7 @@ def test_degenerate_pattern_sets():
 
 @pytest.mark.parametrize("seed,alphabet,npat,lo,hi,deep_k", [
     (20, 4, 3000, 12, 24, 12), (21, 3, 800, 14, 20, 13), (22, 26, 2000, 8, 16, 5),
+    (23, 200, 2000, 4, 10, 3), (24, 128, 2000, 3, 9, 3), (25, 64, 1500, 5, 9, 4),
 ])
 def test_deep_level(seed, alphabet, npat, lo, hi, deep_k):
     """Byte-class tries get a packed-class filter in shared memory and a deep
@@ -198,7 +212,7 @@ def test_deep_level(seed, alphabet, npat, lo, hi, deep_k):
     rng = np.random.Generator(np.random.MT19937(seed))
     text = wl.text.copy()
     other = rng.random(len(text)) < 0.002           # bytes on no trie edge
-    text[other] = ord("Z")
+    text[other] = ord("Z") if alphabet <= 26 else 255
     t = pm.pm_build(wl.patterns)
     st = pm.pm_stats(t)
     assert st["deep_k"] == deep_k
@@ -225,6 +239,73 @@ def test_deep_level(seed, alphabet, npat, lo, hi, deep_k):
     b_ids, b_counts, _ = ot.scan_batch(data, off)
     for c in (None, small_cfg(t), dict(cfg, deep=0)):
         ids, counts = batch_gpu(t, bw, c)
+        assert np.array_equal(ids, b_ids) and np.array_equal(counts, b_counts)
+
+
+@pytest.mark.parametrize("seed,alphabet,npat,lo,hi,n", [
+    (40, 2, 30, 1, 9, 9_001), (41, 4, 3000, 14, 24, 40_000), (42, 26, 300, 3, 16, 65_536),
+    (43, 256, 800, 1, 8, 20_003), (44, 200, 1500, 4, 10, 33_333), (45, 256, 3000, 8, 40, 64_000),
+])
+def test_light_form_equals_persistent(seed, alphabet, npat, lo, hi, n):
+    """The light launch form for short texts (small CTAs, filters read from
+    L2, walks in place) and the persistent kernel give the oracle's bits:
+    byte alphabets with exact and Bloom filters, byte classes with and
+    without a deep level, checked, counting and unaligned."""
+    wl = W.random_case(seed, npat, n, alphabet, lo, hi, plant_rate=0.05)
+    t = pm.pm_build(wl.patterns)
+    o_ids, o_cnt, o_look = oracle.Trie(wl.patterns).scan(wl.text)
+    for cfg in (light(t), persistent(t), light(t, checked=1), light(t, deep=0)
+                if pm.pm_stats(t)["deep_k"] else light(t, row_search=1), light(t, layout=1)):
+        ids, cnt, _ = gpu_scan(t, wl.text, cfg=cfg)
+        assert_same(ids, cnt, o_ids, o_cnt)
+    ids, cnt, look = gpu_scan(t, wl.text, cfg=light(t), lookups=True)
+    assert_same(ids, cnt, o_ids, o_cnt)
+    assert look == o_look
+    ids, cnt, _ = gpu_scan(t, wl.text, cfg=light(t), offset=3)
+    assert_same(ids, cnt, o_ids, o_cnt)
+
+
+def test_unary_chains():
+    """Runs of single-child nodes are walked by comparing the text with the
+    run's labels 16 bytes at a time. Texts that leave a run at every offset,
+    runs from the root, patterns that end inside a run (prefixes of longer
+    patterns), runs longer than several 16-byte blocks, a text that ends
+    inside a run, unaligned texts and batches: all against the oracle."""
+    rng = np.random.Generator(np.random.MT19937(77))
+    base = [rng.integers(0, 256, size=L, dtype=np.uint8).tobytes() for L in (3, 17, 40, 100, 301)]
+    cases = [
+        base + [b[:k] for b in base[2:] for k in (5, 16, 33)],   # finals inside runs
+        [base[4]],                                               # one run from the root
+        [b"ACGT" * 8 + b"A", b"ACGT" * 8 + b"C", b"ACGTACGA"],   # small alphabet
+    ]
+    for pats in cases:
+        pieces = []
+        for b in pats:
+            for k in range(len(b)):                    # leave the run at offset k
+                x = bytearray(b)
+                x[k] ^= 0x5A
+                pieces.append(bytes(x))
+            pieces.append(b)
+        filler = rng.integers(0, 256, size=5000, dtype=np.uint8).tobytes()
+        text = np.frombuffer(b"".join(pieces) + filler + pats[-1][:-1], np.uint8)
+        t = pm.pm_build(pats)
+        ot = oracle.Trie(pats)
+        o_ids, o_cnt, _ = ot.scan(text)
+        assert o_cnt > 0
+        cfg = pm.pm_get_config(t)
+        for c in (None, dict(cfg, positions=4), dict(cfg, checked=1), dict(cfg, layout=1),
+                  small_cfg(t), dict(cfg, row_search=1)):
+            ids, cnt, _ = gpu_scan(t, text, cfg=c)
+            assert_same(ids, cnt, o_ids, o_cnt)
+        for off in (1, 2, 3):
+            ids, cnt, _ = gpu_scan(t, text, offset=off)
+            assert_same(ids, cnt, o_ids, o_cnt)
+        # a batch whose texts end inside runs
+        cut = [0, 7, len(pats[0]) - 1, 500, 2001, len(text)]
+        data, off = W.concat([text[a:b] for a, b in zip(cut, cut[1:])])
+        bw = W.Workload("chains", 0, W.PatternSet.from_list(pats), data, off)
+        b_ids, b_counts, _ = ot.scan_batch(data, off)
+        ids, counts = batch_gpu(t, bw)
         assert np.array_equal(ids, b_ids) and np.array_equal(counts, b_counts)
 
 
