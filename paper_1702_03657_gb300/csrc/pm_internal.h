@@ -242,6 +242,13 @@ ScanLayout scan_layout(const TrieDev &t, const pm_config &cfg);
 // Dynamic shared memory the scan needs for a configuration.
 uint64_t scan_smem_bytes(const TrieDev &t, const pm_config &cfg);
 
+// Stream push preparation: dst = carry[0 .. nc) || chunk[0 .. len); bytes
+// [keep_from, keep_from + nkeep) of dst also to carry_out (which must not
+// overlap carry); *count = 0. Asynchronous on `stream`.
+int launch_gather(const uint8_t *carry, uint64_t nc, const uint8_t *chunk, uint64_t len,
+                  uint8_t *dst, uint8_t *carry_out, uint64_t keep_from, uint64_t nkeep,
+                  int64_t *count, void *stream, std::string &msg);
+
 // Reads and clears the device error word.
 int read_device_error(int *code, std::string &msg);
 

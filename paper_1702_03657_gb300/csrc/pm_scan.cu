@@ -105,6 +105,7 @@ struct KParams {
     uint32_t aligned;
     uint32_t ids_aligned;
     long long wait_budget;      // SM clocks per TMA wait
+    uint32_t light_add;         // light form, one CTA: add to the count, not overwrite
     // shared-memory layout (byte offsets)
     uint32_t off_lut, off_warp;   // class table, then the per-warp blocks
     uint32_t warp_bytes;          // bytes of one warp's block
@@ -790,6 +791,8 @@ __global__ void __launch_bounds__(1024, 1) pfac_scan_kernel(const KParams p)
                                     rootm |= 1u << q;
                                 }
                             if (DC > FC && need) {
+                                // the D-gram's bit in the deep level (L2):
+                                // all loads issued, then tested
                                 uint32_t dw[P];
 #pragma unroll
                                 for (int q = 0; q < P; ++q) {
@@ -1097,16 +1100,22 @@ KernelFn pick_kernel(const TrieDev &t, uint32_t k, uint32_t gram, uint32_t D, bo
 }
 
 // Light form for short single texts: no shared-memory tables, no staging,
-// small CTAs, four positions per thread. Each position reads its bytes
-// through L1, tests the filter word in global memory (L2-resident), writes
-// -1, and walks at once when the filter cannot rule it out; the same
-// filters, start nodes and walks as the persistent kernel, so the same bits.
-// Launching it costs a few microseconds where the persistent kernel loads
+// kLightThreads threads a CTA, four positions per thread. A thread loads its
+// bytes, then the filter words of its four positions (global memory,
+// L2-resident) all at once, writes -1, and walks at once where the filter
+// cannot rule a position out: the same filters, start nodes and walks as
+// the persistent kernel, so the same bits. A text that one CTA covers gets
+// its count written by that CTA (no separate zeroing of the count);
+// launching it costs a few microseconds where the persistent kernel loads
 // up to 128 KiB of tables into every CTA first.
+constexpr uint32_t kLightThreads = 512;
+constexpr uint32_t kLightP = 4;
+
 template <int KF, int G, bool IDENT, int MODE>
-__global__ void __launch_bounds__(256) pfac_light_kernel(const KParams p)
+__global__ void __launch_bounds__(kLightThreads) pfac_light_kernel(const KParams p)
 {
-    constexpr int P = 4;
+    constexpr int P = (int)kLightP;
+    __shared__ unsigned long long s_red[kLightThreads / 32];
     const TrieDev &t = p.t;
     const uint64_t pol = policy_evict_last();
     const uint32_t lane = threadIdx.x & 31;
@@ -1114,42 +1123,68 @@ __global__ void __launch_bounds__(256) pfac_light_kernel(const KParams p)
     const unsigned long long i0 = ((unsigned long long)blockIdx.x * blockDim.x + threadIdx.x) * P;
     constexpr uint32_t KFU = KF > 0 ? (uint32_t)KF : 0u;
     const uint32_t cb = p.cb;
-    for (int q = 0; q < P; ++q) {
-        const unsigned long long pos = i0 + q;
-        if (pos >= p.total) break;
-        __stcs(p.ids + pos, -1);
-        const unsigned long long left = p.limit - pos;  // readable bytes from pos
-        const uint8_t *tp = p.text + pos;
-        unsigned long long e = pos;  // root walk unless the filter says otherwise
-        uint32_t code = 0;
-        bool walk = true;
-        if (MODE != MODE_LOOKUPS && p.gram <= left) {
-            if (IDENT) {
-                uint32_t x = 0;
-                for (uint32_t j = 0; j < p.gram; ++j) x |= (uint32_t)__ldg(tp + j) << (8 * j);
-                uint32_t word, bits;
+    if (i0 < p.total) {
+        const uint8_t *tp = p.text + i0;
+        const unsigned long long left0 = p.limit - i0;  // readable bytes from i0
+        unsigned long long e[P];
+        uint32_t code[P];
+        uint32_t walk = 0;  // bit q: position i0+q is walked
+#pragma unroll
+        for (int q = 0; q < P; ++q) {
+            e[q] = i0 + q;
+            code[q] = 0;
+        }
+        if (IDENT && MODE != MODE_LOOKUPS) {
+            // bytes i0 .. i0 + P + 2 (those inside the readable text)
+            uint32_t b[P + 3];
+#pragma unroll
+            for (int j = 0; j < P + 3; ++j) b[j] = (unsigned long long)j < left0 ? __ldg(tp + j) : 0u;
+            uint32_t word[P], bits[P];
+#pragma unroll
+            for (int q = 0; q < P; ++q) {
+                const uint32_t x = b[q] | (b[q + 1] << 8) | (b[q + 2] << 16) | (b[q + 3] << 24);
                 if (KF >= (int)kBloomK) {
-                    const BloomProbe b = bloom_probe(x, p.gram, 8u * KFU + p.lw - 5u);
-                    word = b.word;
-                    bits = b.mask;
+                    const BloomProbe pr = bloom_probe(x, p.gram, 8u * KFU + p.lw - 5u);
+                    word[q] = pr.word;
+                    bits[q] = pr.mask;
                 } else {
                     const uint32_t idx = x & (uint32_t)((1ull << (8 * KFU + p.lw)) - 1ull);
-                    word = idx >> 5;
-                    bits = 1u << (idx & 31u);
+                    word[q] = idx >> 5;
+                    bits[q] = 1u << (idx & 31u);
                 }
-                if (MODE == MODE_CHECKED && word >= p.filt_words) {
+                if (MODE == MODE_CHECKED && word[q] >= p.filt_words) {
                     record_error(PM_ERR_BOUNDS);
+                    word[q] = 0;
+                    bits[q] = 0;
+                }
+                if (KF >= 1) code[q] = KF == 1 ? b[q] : (b[q] << 8) | b[q + 1];
+            }
+            uint32_t fw[P];
+#pragma unroll
+            for (int q = 0; q < P; ++q) fw[q] = ld_trie_u32(p.filter + word[q], pol);
+#pragma unroll
+            for (int q = 0; q < P; ++q) {
+                if (i0 + q >= p.total) break;
+                if ((unsigned long long)q + p.gram > left0) {
+                    walk |= 1u << q;  // too close to the end to test: from the root
+                } else if ((fw[q] & bits[q]) == bits[q]) {
+                    walk |= 1u << q;
+                    if (KF >= 1) e[q] |= (unsigned long long)WALK_DENSE << 61;
+                }
+            }
+        } else {
+#pragma unroll
+            for (int q = 0; q < P; ++q) {
+                if (i0 + q >= p.total) break;
+                const unsigned long long left = left0 - q;
+                if (MODE == MODE_LOOKUPS || p.F == 0 || p.gram > left) {
+                    walk |= 1u << q;
                     continue;
                 }
-                walk = (ld_trie_u32(p.filter + word, pol) & bits) == bits;
-                if (walk && KF >= 1) {
-                    code = KF == 1 ? (x & 0xFFu) : ((x & 0xFFu) << 8) | ((x >> 8) & 0xFFu);
-                    e = pos | ((unsigned long long)WALK_DENSE << 61);
-                }
-            } else if (p.F > 0) {
+                const uint8_t *pq = tp + q;
                 uint32_t c = 0, oth = 0;
                 for (uint32_t j = 0; j < p.F; ++j) {
-                    const uint32_t v = __ldg(t.cls + __ldg(tp + j));
+                    const uint32_t v = __ldg(t.cls + __ldg(pq + j));
                     c = (c << cb) | (v & ((1u << cb) - 1u));
                     oth |= v & 0x80u;
                 }
@@ -1158,26 +1193,47 @@ __global__ void __launch_bounds__(256) pfac_light_kernel(const KParams p)
                     record_error(PM_ERR_BOUNDS);
                     continue;
                 }
-                walk = (ld_trie_u32(p.filter + (c >> 5), pol) >> (c & 31u)) & 1u;
-                if (walk && p.D > 0 && p.D <= left) {
+                if (!((ld_trie_u32(p.filter + (c >> 5), pol) >> (c & 31u)) & 1u)) continue;
+                walk |= 1u << q;
+                if (p.D > 0 && p.D <= left) {
                     for (uint32_t j = p.F; j < p.D; ++j) {
-                        const uint32_t v = __ldg(t.cls + __ldg(tp + j));
+                        const uint32_t v = __ldg(t.cls + __ldg(pq + j));
                         c = (c << cb) | (v & ((1u << cb) - 1u));
                         oth |= v & 0x80u;
                     }
-                    if (t.other_check && oth) continue;
-                    code = c;
-                    e = pos | ((unsigned long long)WALK_DEEP << 61);
+                    if (t.other_check && oth) {
+                        walk &= ~(1u << q);
+                        continue;
+                    }
+                    code[q] = c;
+                    e[q] |= (unsigned long long)WALK_DEEP << 61;
                 }
             }
         }
-        if (walk) run_walk<false, MODE>(p, e, code, p.limit, pol, acc, look, nwalk);
+#pragma unroll
+        for (int q = 0; q < P; ++q)
+            if (i0 + q < p.total) __stcs(p.ids + i0 + q, -1);
+#pragma unroll
+        for (int q = 0; q < P; ++q)
+            if ((walk >> q) & 1u) run_walk<false, MODE>(p, e[q], code[q], p.limit, pol, acc, look, nwalk);
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         acc += __shfl_xor_sync(kFull, acc, o);
         look += __shfl_xor_sync(kFull, look, o);
         nwalk += __shfl_xor_sync(kFull, nwalk, o);
+    }
+    if (gridDim.x == 1) {
+        // one CTA: it writes the count (and adds the lookups and walks) itself
+        if (lane == 0) s_red[threadIdx.x >> 5] = acc;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            unsigned long long tot = 0;
+            for (uint32_t w = 0; w < (blockDim.x >> 5); ++w) tot += s_red[w];
+            if (p.light_add) *p.counts += (int64_t)tot;
+            else *p.counts = (int64_t)tot;
+        }
+        acc = 0;
     }
     if (lane == 0) {
         if (acc) atomicAdd(reinterpret_cast<unsigned long long *>(p.counts), acc);
@@ -1281,7 +1337,11 @@ int launch_scan(const TrieDev &t, const pm_config &cfg, const ScanArgs &a, void 
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     const bool batch = a.offsets != nullptr;
     const uint32_t ncount = batch ? a.ntexts : 1;
-    if (ncount && !a.keep_counts) {
+    // the light form on a text one CTA covers writes its count itself
+    const bool light1 = !batch && cfg.light_max > 0 && a.len > 0 &&
+                        a.len <= (uint64_t)cfg.light_max &&
+                        a.len <= (uint64_t)kLightThreads * kLightP && !a.lookups;
+    if (ncount && !a.keep_counts && !light1) {
         cudaError_t e = cudaMemsetAsync(a.counts, 0, sizeof(int64_t) * ncount, st);
         if (e != cudaSuccess) {
             msg = std::string("cudaMemsetAsync: ") + cudaGetErrorString(e);
@@ -1353,9 +1413,10 @@ int launch_scan(const TrieDev &t, const pm_config &cfg, const ScanArgs &a, void 
 
     cudaError_t e;
     if (!batch && c.light_max > 0 && a.len <= (uint64_t)c.light_max) {
-        const uint32_t threads = 128;
-        const unsigned long long per = 4ull * threads;
-        const unsigned long long grid = (a.len + per - 1) / per;
+        const uint32_t threads = kLightThreads;
+        const unsigned long long per = (unsigned long long)kLightP * threads;
+        const unsigned long long grid = light1 ? 1ull : (a.len + per - 1) / per;
+        p.light_add = a.keep_counts ? 1u : 0u;
         KernelFn lf = pick_light(t, (uint32_t)c.dense_k, ident ? t.gram[c.dense_k] : 0u, mode);
         lf<<<(unsigned)grid, threads, 0, st>>>(p);
         e = cudaGetLastError();

@@ -127,25 +127,17 @@ int pm_scanner_push(pm_scanner *s, const uint8_t *d_chunk, uint64_t len, int32_t
             s->d_buf = static_cast<uint8_t *>(nb);
             s->buf_cap = cap;
         }
-        if (carry > 0) {
-            e = cudaMemcpyAsync(s->d_buf, s->d_carry[s->cur], carry, cudaMemcpyDeviceToDevice, st);
-            if (e != cudaSuccess) return scuda("cudaMemcpyAsync", e);
-        }
-        e = cudaMemcpyAsync(s->d_buf + carry, d_chunk, len, cudaMemcpyDeviceToDevice, st);
-        if (e != cudaSuccess) return scuda("cudaMemcpyAsync", e);
-        if (held + fresh > 0) {
-            const int rc = scan_piece(s->h, s->d_buf, held + fresh, carry + len, d_ids, d_count,
-                                      false, st);
-            if (rc != PM_OK) return rc;
-        } else {
-            e = cudaMemsetAsync(d_count, 0, sizeof(int64_t), st);
-            if (e != cudaSuccess) return scuda("cudaMemsetAsync", e);
-        }
+        // one launch: carry || chunk into the buffer, the next carry (bytes
+        // [Rn, Ln) of the stream) saved, the count zeroed; then one scan
+        // that adds to the count
         const uint64_t nc = Ln - Rn;
-        if (nc > 0) {
-            e = cudaMemcpyAsync(s->d_carry[s->cur ^ 1], s->d_buf + (Rn - R), nc,
-                                cudaMemcpyDeviceToDevice, st);
-            if (e != cudaSuccess) return scuda("cudaMemcpyAsync", e);
+        std::string msg;
+        int rc = pm::launch_gather(s->d_carry[s->cur], carry, d_chunk, len, s->d_buf,
+                                   s->d_carry[s->cur ^ 1], Rn - R, nc, d_count, st, msg);
+        if (rc != PM_OK) return sfail(rc, msg);
+        if (held + fresh > 0) {
+            rc = scan_piece(s->h, s->d_buf, held + fresh, carry + len, d_ids, d_count, true, st);
+            if (rc != PM_OK) return rc;
         }
         s->cur ^= 1;
         s->L = Ln;
