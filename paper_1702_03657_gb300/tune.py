@@ -30,8 +30,9 @@ def candidates(trie: pm.Trie, total_bytes: int, single: bool = False) -> List[di
     ident = st["alphabet"] == 256
     widths = (8, 16, 32) if ident else (8,)
     # small inputs cannot fill large CTAs: smaller ones launch and start faster
-    threads = [base["threads"], 512] + ([256, 128] if total_bytes <= (4 << 20) else [])
-    tiles = (256, 1024, 2048) if total_bytes <= (4 << 20) else (1024, 2048, 4096)
+    threads = list(dict.fromkeys([base["threads"], 1024, 992, 896, 512] +
+                                 ([256, 128] if total_bytes <= (4 << 20) else [])))
+    tiles = (256, 1024, 2048) if total_bytes <= (4 << 20) else (512, 1024, 2048)
     lights = (0, 1 << 30) if single and total_bytes <= (1 << 20) else (0,)
     out, seen = [], set()
     for th, tile, stages, k, bits, pos, rs, lm in itertools.product(
