@@ -225,6 +225,14 @@ void fill_dev_sizes(pm_trie *h)
     d.dense_k_max = t.dense_k_max;
     d.cb = t.cb;
     d.other_check = t.other_check;
+    d.sw_shift = t.sw_shift;
+    for (int w = 0; w < 2; ++w) {
+        d.sw_cls[w] = d.sw_sym[w] = 0;
+        for (int j = 0; j < 4; ++j) {
+            d.sw_cls[w] |= (uint32_t)t.sw_cls[4 * w + j] << (8 * j);
+            d.sw_sym[w] |= (uint32_t)t.sw_sym[4 * w + j] << (8 * j);
+        }
+    }
     d.deep_k = t.deep_k;
     d.deep_first = t.deep_first;
     d.deep_words = (uint32_t)(t.deep.size() / 2);

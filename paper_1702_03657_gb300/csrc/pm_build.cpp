@@ -162,6 +162,30 @@ int build_class_tables(HostTrie &t, uint32_t nn, const std::vector<uint32_t> &lv
         const uint32_t c = t.cls[b];
         t.lut[b] = c < U ? (uint8_t)c : (uint8_t)(t.other_check ? 0x80u : U);
     }
+    if (cb == 2 && U == 4) {
+        for (uint32_t s = 0; s <= 5 && t.sw_shift == kNoSwar; ++s) {
+            uint32_t seen = 0;
+            bool ok = true;
+            for (int b = 0; b < 256 && ok; ++b)
+                if (t.cls[b] < U) {
+                    const uint32_t f = ((uint32_t)b >> s) & 7u;
+                    ok = !((seen >> f) & 1u);
+                    seen |= 1u << f;
+                }
+            if (!ok) continue;
+            t.sw_shift = s;
+            for (uint32_t f = 0; f < 8; ++f) {
+                t.sw_cls[f] = 0;
+                t.sw_sym[f] = (uint8_t)((f ^ 1u) << s);  // field f ^ 1: matches no byte of field f
+            }
+            for (int b = 0; b < 256; ++b)
+                if (t.cls[b] < U) {
+                    const uint32_t f = ((uint32_t)b >> s) & 7u;
+                    t.sw_cls[f] = (uint8_t)t.cls[b];
+                    t.sw_sym[f] = (uint8_t)b;
+                }
+        }
+    }
     const uint32_t FM = m ? std::min<uint32_t>({t.min_len, kFilterCodeBits / cb, (uint32_t)kMaxDenseK}) : 0;
     const uint32_t D = m ? std::min<uint32_t>(t.min_len, kDeepCodeBits / cb) : 0;
     t.dense_k_max = FM;
@@ -386,6 +410,9 @@ int build_host_trie(const uint8_t *const *patterns, const uint32_t *lengths,
     t.deep.clear();
     t.cb = t.other_check = 0;
     std::memset(t.lut, 0, sizeof(t.lut));
+    t.sw_shift = kNoSwar;
+    std::memset(t.sw_cls, 0, sizeof(t.sw_cls));
+    std::memset(t.sw_sym, 0, sizeof(t.sw_sym));
     std::vector<uint32_t> lvl_begin(t.max_len + 2, nn), lvl_count(t.max_len + 2, 0);
     for (uint32_t v = 0; v < nn; ++v)
         if (lvl_count[t.depth[v]]++ == 0) lvl_begin[t.depth[v]] = v;

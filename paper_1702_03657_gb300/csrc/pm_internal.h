@@ -103,6 +103,8 @@ __host__ __device__ inline BloomProbe bloom_probe(uint32_t x, uint32_t gram, uin
 //   y: row length (bits 0..8) | 1 << 31 when a pattern ends on v's path
 //   z, w: the row's first eight column bytes, ascending (zero padded)
 // col holds every row's bytes for rows longer than eight.
+constexpr uint32_t kNoSwar = 0xFFu;  // no 3-bit field tells the four letters apart
+
 struct TrieDev {
     const uint4 *row;
     const uint8_t *col;
@@ -123,6 +125,11 @@ struct TrieDev {
     uint32_t dense_k_max;                                 // deepest filter level
     uint32_t cb;                                          // byte classes: bits per class
     uint32_t other_check;                                 // byte classes: U == 2^cb
+    // byte classes, four letters: the class of a byte read from an 8-entry
+    // byte table by a 3-bit field of the byte (see HostTrie)
+    uint32_t sw_shift;                                    // field (b >> sw_shift) & 7, or kNoSwar
+    uint32_t sw_cls[2];                                   // field -> class
+    uint32_t sw_sym[2];                                   // field -> the letter with that field
     const uint2 *deep;                                    // deep level {bits, base} (or null)
     uint32_t deep_k;                                      // its depth D (0: none)
     uint32_t deep_first;                                  // BFS id of the first depth-D node
@@ -155,6 +162,13 @@ struct HostTrie {
     // gets U, or 0x80 (flag, class bits 0) with other_check
     uint8_t lut[256];
     uint32_t cb = 0, other_check = 0;
+    // four letters (U == 4): a shift s such that (b >> s) & 7 differs for
+    // the four letters, and two 8-byte tables over that field: the letter's
+    // class, and the letter itself (a field no letter has holds a byte whose
+    // field differs, so that no byte matches it). A byte is a letter iff it
+    // equals the table's letter at its field. kNoSwar: no such shift.
+    uint32_t sw_shift = kNoSwar;
+    uint8_t sw_cls[8] = {}, sw_sym[8] = {};
     uint32_t C = 0;
     uint32_t min_len = 0, max_len = 0;
     uint64_t n_patterns = 0, n_duplicates = 0;

@@ -551,6 +551,42 @@ __device__ __forceinline__ uint32_t classify(const uint8_t *st, const uint32_t *
     return c;
 }
 
+// Shifts bit 0 of r in at the top of acc: after P steps the first step's bit
+// is at bit 32 - P and the last's at bit 31, so acc >> (32 - P) has step q's
+// bit at bit q.
+__device__ __forceinline__ uint32_t funnel_in(uint32_t acc, uint32_t r)
+{
+    return __funnelshift_r(acc, r, 1);
+}
+
+// classify for four letters told apart by the field f = (b >> sh) & 7, four
+// bytes at a time: the fields of a word become a byte-permute selector, which
+// reads each byte's class and letter out of the 8-byte tables (cl, sy). A
+// byte that differs from its field's letter is of no pattern (oth = 1). The
+// four 2-bit classes are packed first byte highest by one multiply: class j
+// sits at bit 8j and is moved to bit 30 - 2j, and no two partial products
+// overlap in bits 24..31.
+template <int P>
+__device__ __forceinline__ uint32_t classify4(const uint8_t *st, uint32_t sh, uint32_t cl0,
+                                              uint32_t cl1, uint32_t sy0, uint32_t sy1,
+                                              uint32_t &oth)
+{
+    uint32_t c = 0;
+    bool bad = false;
+#pragma unroll
+    for (int w = 0; w < P / 4; ++w) {
+        const uint32_t word = *reinterpret_cast<const uint32_t *>(st + 4 * w);
+        const uint32_t f = (word >> sh) & 0x07070707u;
+        // byte j of f | f >> 4 holds f_j | f_{j+1} << 4: bytes 0 and 2
+        // give the four selector nibbles
+        const uint32_t sel = __byte_perm(f | (f >> 4), 0u, 0x20u);
+        bad |= __byte_perm(sy0, sy1, sel) != word;
+        c = (c << 8) | ((__byte_perm(cl0, cl1, sel) * 0x40100401u) >> 24);
+    }
+    oth = bad ? 1u : 0u;
+    return c;
+}
+
 // KF: the byte alphabet's filter level k (0, 1, 2), or -1 for byte classes.
 // G: bytes the byte alphabet's Bloom filter tests (3 or 4), 0 otherwise.
 // P: start positions per lane and group.
@@ -638,6 +674,8 @@ __global__ void __launch_bounds__(1024, 1) pfac_scan_kernel(const KParams p)
         const uint32_t cb = CB ? (uint32_t)CB : p.cb, Pcb = P * cb;
         const uint32_t Fv = FIXED ? (uint32_t)FC : p.F, Dv = FIXED ? (uint32_t)DC : p.D;
         const uint32_t nnb = FIXED ? NNBC : p.nnb;
+        // four letters with a telling 3-bit field (fixed shapes only)
+        const bool sw = FIXED && t.sw_shift != kNoSwar;
         const uint32_t shF = 32u - cb * Fv, shD = 32u - cb * Dv;  // used only when F, D > 0
         const uint32_t span = (p.gram > 1 ? p.gram : 1u) - 1u;  // bytes a position's filter reads past it
         bool failed = false;
@@ -688,7 +726,10 @@ __global__ void __launch_bounds__(1024, 1) pfac_scan_kernel(const KParams p)
             // byte classes: the lane's chunk of the current group (carried
             // from the previous group's look-ahead)
             uint32_t cur_c = 0, cur_o = 0;
-            if (!IDENT) cur_c = classify<P>(st + P * lane, s_lut, lane, cb, cur_o);
+            if (!IDENT)
+                cur_c = sw ? classify4<P>(st + P * lane, t.sw_shift, t.sw_cls[0], t.sw_cls[1],
+                                          t.sw_sym[0], t.sw_sym[1], cur_o)
+                           : classify<P>(st + P * lane, s_lut, lane, cb, cur_o);
 
             const uint32_t iters = (tile_n + GP - 1) / GP;
             for (uint32_t i = 0; i < iters; ++i) {
@@ -712,7 +753,9 @@ __global__ void __launch_bounds__(1024, 1) pfac_scan_kernel(const KParams p)
                     // within the stage buffer; bytes past the staged ones
                     // only reach codes of positions that take the slow path)
                     if (lp0 + GP + P <= p.stage_bytes)
-                        nxt_c = classify<P>(st + lp0 + GP, s_lut, lane, cb, nxt_o);
+                        nxt_c = sw ? classify4<P>(st + lp0 + GP, t.sw_shift, t.sw_cls[0], t.sw_cls[1],
+                                                  t.sw_sym[0], t.sw_sym[1], nxt_o)
+                                   : classify<P>(st + lp0 + GP, s_lut, lane, cb, nxt_o);
                     X = (uint64_t)cur_c << (64u - Pcb);
 #pragma unroll
                     for (int d = 1; d <= kMaxNeighbours; ++d) {
@@ -738,33 +781,41 @@ __global__ void __launch_bounds__(1024, 1) pfac_scan_kernel(const KParams p)
                             // blocked Bloom test of the g-gram at each position
                             const uint32_t sh = 32u - (8u * KFU + lw - 5u);
                             const uint32_t gsh = G > 0 ? 32u - 8u * G : 32u - 8u * p.gram;
+                            uint32_t acc_f = 0;  // see funnel_in
 #pragma unroll
                             for (int q = 0; q < P; ++q) {
                                 const uint32_t win = PM_WIN(q);
                                 // bytes q .. q+g-1, shifted to the top
                                 const uint32_t h = __umulhi(G == 4 ? win : win << gsh, kBloomMul);
                                 const uint32_t word = h >> sh;
+                                uint32_t r = 0;
                                 if (MODE == MODE_CHECKED && word >= p.filt_words) {
                                     record_error(PM_ERR_BOUNDS);
-                                    continue;
+                                } else {
+                                    // both Bloom bits, each rotated down to bit 0 (the
+                                    // funnel shift takes its amount mod 32)
+                                    const uint32_t val = s_filt[word];
+                                    r = __funnelshift_r(val, val, h) & __funnelshift_r(val, val, h >> 5);
                                 }
-                                // both Bloom bits, each rotated down to bit 0 (the
-                                // funnel shift takes its amount mod 32)
-                                const uint32_t val = s_filt[word];
-                                const uint32_t r = __funnelshift_r(val, val, h) & __funnelshift_r(val, val, h >> 5);
-                                need |= (r & 1u) << q;
+                                acc_f = funnel_in(acc_f, r);
                             }
+                            need = acc_f >> (32 - P);
                         } else if (KF >= 0) {
+                            uint32_t acc_f = 0;
 #pragma unroll
                             for (int q = 0; q < P; ++q) {
                                 const uint32_t idx = PM_WIN(q) & imask;
                                 const uint32_t word = idx >> 5;
+                                uint32_t r = 0;
                                 if (MODE == MODE_CHECKED && word >= p.filt_words) {
                                     record_error(PM_ERR_BOUNDS);
-                                    continue;
+                                } else {
+                                    const uint32_t val = s_filt[word];
+                                    r = __funnelshift_r(val, val, idx);
                                 }
-                                need |= ((s_filt[word] >> (idx & 31u)) & 1u) << q;
+                                acc_f = funnel_in(acc_f, r);
                             }
+                            need = acc_f >> (32 - P);
                         }
                         if (KF == 0) {  // no dense level: passing positions walk from the root
                             rootm = need;
@@ -773,26 +824,39 @@ __global__ void __launch_bounds__(1024, 1) pfac_scan_kernel(const KParams p)
                     } else if (FIXED) {
                         // byte classes, shapes fixed at compile time: every
                         // code is a constant shift of the window
+                        // (a code's low 5 bits, the bit in its word, are the
+                        // low bits of the shifted window: the rotations below
+                        // take their amount mod 32)
                         constexpr uint32_t FM = (1u << (CB * FC)) - 1u, DM = (1u << (CB * DC)) - 1u;
+                        uint32_t acc_f = 0;
 #pragma unroll
                         for (int q = 0; q < P; ++q) {
-                            const uint32_t code = (uint32_t)(X >> (64 - CB * (q + FC))) & FM;
-                            if (MODE == MODE_CHECKED && (code >> 5) >= p.filt_words) {
+                            const uint32_t a = (uint32_t)(X >> (64 - CB * (q + FC)));
+                            uint32_t r = 0;
+                            if (MODE == MODE_CHECKED && ((a & FM) >> 5) >= p.filt_words) {
                                 record_error(PM_ERR_BOUNDS);
-                                continue;
+                            } else {
+                                const uint32_t val = s_filt[(a & FM) >> 5];
+                                r = __funnelshift_r(val, val, a);
                             }
-                            need |= ((s_filt[code >> 5] >> (code & 31u)) & 1u) << q;
+                            acc_f = funnel_in(acc_f, r);
                         }
+                        need = acc_f >> (32 - P);
                         if (need) {
+                            if (lp0 + (P - 1) + DC > rel_end) {
+                                // positions whose D-gram leaves the text walk
+                                // from the root
 #pragma unroll
-                            for (int q = 0; q < P; ++q)
-                                if (((need >> q) & 1u) && lp0 + q + DC > rel_end) {
-                                    need &= ~(1u << q);
-                                    rootm |= 1u << q;
-                                }
+                                for (int q = 0; q < P; ++q)
+                                    if (((need >> q) & 1u) && lp0 + q + DC > rel_end) {
+                                        need &= ~(1u << q);
+                                        rootm |= 1u << q;
+                                    }
+                            }
                             if (DC > FC && need) {
                                 // the D-gram's bit in the deep level (L2):
-                                // all loads issued, then tested
+                                // all loads issued, then tested (a position
+                                // not tested keeps word 0: bit clear)
                                 uint32_t dw[P];
 #pragma unroll
                                 for (int q = 0; q < P; ++q) {
@@ -801,36 +865,41 @@ __global__ void __launch_bounds__(1024, 1) pfac_scan_kernel(const KParams p)
                                     const uint32_t code = (uint32_t)(X >> (64 - CB * (q + DC))) & DM;
                                     if (MODE == MODE_CHECKED && (code >> 5) >= t.deep_words) {
                                         record_error(PM_ERR_BOUNDS);
-                                        need &= ~(1u << q);
                                         continue;
                                     }
                                     dw[q] = ld_trie_u32(t.deep + (code >> 5), pol);
                                 }
+                                uint32_t acc_d = 0;
 #pragma unroll
                                 for (int q = 0; q < P; ++q) {
-                                    const uint32_t code = (uint32_t)(X >> (64 - CB * (q + DC))) & DM;
-                                    if (((need >> q) & 1u) && !((dw[q] >> (code & 31u)) & 1u))
-                                        need &= ~(1u << q);
+                                    const uint32_t a = (uint32_t)(X >> (64 - CB * (q + DC)));
+                                    acc_d = funnel_in(acc_d, __funnelshift_r(dw[q], dw[q], a));
                                 }
+                                need = acc_d >> (32 - P);
                             }
                         }
                     } else {
                         // byte classes: the F-gram at each position in the
                         // exact shared-memory bitmap
-                        uint64_t Xq = X;
+                        if (p.F == 0) {
+                            need = (1u << P) - 1u;
+                        } else {
+                            uint64_t Xq = X;
+                            uint32_t acc_f = 0;
 #pragma unroll
-                        for (int q = 0; q < P; ++q) {
-                            if (p.F == 0) {
-                                need |= 1u << q;
-                                continue;
+                            for (int q = 0; q < P; ++q) {
+                                const uint32_t code = (uint32_t)(Xq >> 32) >> shF;
+                                Xq <<= cb;
+                                uint32_t r = 0;
+                                if (MODE == MODE_CHECKED && (code >> 5) >= p.filt_words) {
+                                    record_error(PM_ERR_BOUNDS);
+                                } else {
+                                    const uint32_t val = s_filt[code >> 5];
+                                    r = __funnelshift_r(val, val, code);
+                                }
+                                acc_f = funnel_in(acc_f, r);
                             }
-                            const uint32_t code = (uint32_t)(Xq >> 32) >> shF;
-                            Xq <<= cb;
-                            if (MODE == MODE_CHECKED && (code >> 5) >= p.filt_words) {
-                                record_error(PM_ERR_BOUNDS);
-                                continue;
-                            }
-                            need |= ((s_filt[code >> 5] >> (code & 31u)) & 1u) << q;
+                            need = acc_f >> (32 - P);
                         }
                         if (need) {
                             if (p.D == 0) {
@@ -839,15 +908,18 @@ __global__ void __launch_bounds__(1024, 1) pfac_scan_kernel(const KParams p)
                             } else {
                                 // positions whose D-gram leaves the text walk
                                 // from the root
+                                if (lp0 + (P - 1) + p.D > rel_end) {
 #pragma unroll
-                                for (int q = 0; q < P; ++q)
-                                    if (((need >> q) & 1u) && lp0 + q + p.D > rel_end) {
-                                        need &= ~(1u << q);
-                                        rootm |= 1u << q;
-                                    }
+                                    for (int q = 0; q < P; ++q)
+                                        if (((need >> q) & 1u) && lp0 + q + p.D > rel_end) {
+                                            need &= ~(1u << q);
+                                            rootm |= 1u << q;
+                                        }
+                                }
                                 if (p.D > p.F && need) {
                                     // the D-gram's bit in the deep level (L2):
-                                    // all loads issued, then tested
+                                    // all loads issued, then tested (a
+                                    // position not tested keeps word 0)
                                     uint32_t dw[P];
 #pragma unroll
                                     for (int q = 0; q < P; ++q) {
@@ -856,17 +928,17 @@ __global__ void __launch_bounds__(1024, 1) pfac_scan_kernel(const KParams p)
                                         const uint32_t code = (uint32_t)((X << (cb * q)) >> 32) >> shD;
                                         if (MODE == MODE_CHECKED && (code >> 5) >= t.deep_words) {
                                             record_error(PM_ERR_BOUNDS);
-                                            need &= ~(1u << q);
                                             continue;
                                         }
                                         dw[q] = ld_trie_u32(t.deep + (code >> 5), pol);
                                     }
+                                    uint32_t acc_d = 0;
 #pragma unroll
                                     for (int q = 0; q < P; ++q) {
                                         const uint32_t code = (uint32_t)((X << (cb * q)) >> 32) >> shD;
-                                        if (((need >> q) & 1u) && !((dw[q] >> (code & 31u)) & 1u))
-                                            need &= ~(1u << q);
+                                        acc_d = funnel_in(acc_d, __funnelshift_r(dw[q], dw[q], code));
                                     }
+                                    need = acc_d >> (32 - P);
                                 }
                             }
                         }

@@ -265,6 +265,49 @@ def test_light_form_equals_persistent(seed, alphabet, npat, lo, hi, n):
     assert_same(ids, cnt, o_ids, o_cnt)
 
 
+@pytest.mark.parametrize("letters", [b"ACGT", bytes([0, 8, 16, 24]), bytes([0, 1, 0x40, 0x41]),
+                                     bytes([7, 15, 23, 255]), b"TGCA"])
+def test_four_letter_alphabets(letters):
+    """Four letters and patterns of 13 or more: 2-bit classes, filter depth
+    10 and deep level 13 fixed at compile time. Letter sets that a 3-bit
+    field of the byte tells apart (ACGT: the low three bits; 0, 8, 16, 24
+    and 7, 15, 23, 255: bits 2..4) are classified four bytes at a time;
+    others (0, 1, 0x40, 0x41) through the shared-memory table. Bytes of no
+    pattern, among them bytes with a letter's field, are found either way:
+    every id equals the oracle's, single text and batch."""
+    wl = W.random_case(31, 3000, 200_003, 4, 13, 24, plant_rate=0.05)
+    m = np.arange(256, dtype=np.uint8)
+    m[ord("a"):ord("a") + 4] = np.frombuffer(letters, np.uint8)
+    pats = W.PatternSet(m[wl.patterns.data], wl.patterns.off.copy())
+    text = m[wl.text]
+    rng = np.random.Generator(np.random.MT19937(31))
+    others = np.setdiff1d(np.arange(256), np.frombuffer(letters, np.uint8)).astype(np.uint8)
+    pos = np.flatnonzero(rng.random(len(text)) < 0.003)
+    text[pos] = others[rng.integers(0, len(others), size=pos.size)]
+    t = pm.pm_build(pats)
+    st = pm.pm_stats(t)
+    assert st["alphabet"] == 5 and st["deep_k"] == 13
+    cfg = pm.pm_get_config(t)
+    assert cfg["dense_k"] == 10 and cfg["deep"] == 1
+    ot = oracle.Trie(pats)
+    o_ids, o_cnt, _ = ot.scan(text)
+    assert o_cnt > 0
+    for c in (None, persistent(t), persistent(t, positions=4), dict(cfg, checked=1),
+              small_cfg(t, dense_k=10), light(t)):
+        ids, cnt, _ = gpu_scan(t, text, cfg=c)
+        assert_same(ids, cnt, o_ids, o_cnt)
+    pieces, a = [], 0
+    for n in [0, 1, 12, 13, 14, 3, 100, 5000, 16, 2, 70_000]:
+        pieces.append(text[a:a + n])
+        a += n + 5
+    data, off = W.concat(pieces)
+    bw = W.Workload("four_batch", 31, pats, data, off)
+    b_ids, b_counts, _ = ot.scan_batch(data, off)
+    for c in (None, small_cfg(t, dense_k=10)):
+        ids, counts = batch_gpu(t, bw, c)
+        assert np.array_equal(ids, b_ids) and np.array_equal(counts, b_counts)
+
+
 def test_unary_chains():
     """Runs of single-child nodes are walked by comparing the text with the
     run's labels 16 bytes at a time. Texts that leave a run at every offset,
