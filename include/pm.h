@@ -125,7 +125,23 @@ typedef struct {
                           /* light launch form (small CTAs, no shared tables, */
                           /* four positions per thread, walks in place); 0:   */
                           /* never                                            */
+    int32_t schedule;     /* which tiles a warp scans: PM_SCHED_AUTO, _STATIC */
+                          /* or _DYNAMIC (below)                              */
 } pm_config;
+
+/* pm_config.schedule. STATIC: warp w of the grid scans tiles w, w + W,
+ * w + 2W, ... (W warps). DYNAMIC: CTAs take runs of PM_CHUNK_TILES
+ * consecutive tiles from a global counter, in text order, and their warps
+ * take the run's tiles one at a time as they finish one; the whole grid then
+ * sweeps the text as one front and a warp slowed by walks takes fewer tiles.
+ * The counter is 4 bytes of stream-ordered device memory per launch (from a
+ * pool the library keeps); a stream being captured into a graph always
+ * takes STATIC. AUTO: STATIC, which measured as fast or faster on the
+ * workloads this library is tuned on. */
+#define PM_SCHED_AUTO    0
+#define PM_SCHED_STATIC  1
+#define PM_SCHED_DYNAMIC 2
+#define PM_CHUNK_TILES   32u
 
 /* ---- trie construction (Section III, steps I, II, VI and the CRS step) --
  * Builds the trie of patterns[0..n) (lengths[j] bytes each; any byte value,

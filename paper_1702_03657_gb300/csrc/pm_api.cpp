@@ -93,6 +93,18 @@ bool window_fits(const pm_trie *h, const pm_config &c)
 // the byte alphabet's Bloom filter the wider filter comes first (fewer
 // walks); byte-class tries look up the deep level behind their filter. An
 // autotuner may refine it.
+//
+// The shared memory a CTA takes decides how much of the SM's 256 KiB of
+// L1/shared storage stays L1: the driver picks the smallest carveout that
+// holds it (plus 1 KiB per CTA it keeps), in steps ending at 196 and 228
+// KiB. Byte-class tries behind a deep level read the deep level, the trie
+// and the text through L1 for a walk at about one position in a hundred, and
+// measured much faster with the 56 KiB of L1 that the 196 KiB carveout leaves
+// than with the 28 KiB of the 228 KiB one (ACGT, 1 GiB: 2.10 ms with 31
+// warps under 196 KiB, 2.86 ms with 32 warps over it); their configurations
+// stay within it.
+constexpr uint64_t kCarveout196 = 196 * 1024;
+
 pm_config default_config(const pm_trie *h, int smem_limit)
 {
     pm_config c{};
@@ -103,9 +115,11 @@ pm_config default_config(const pm_trie *h, int smem_limit)
     c.layout = 0;
     c.wait_clocks = 0;
     c.light_max = kLightMax;
+    c.schedule = PM_SCHED_AUTO;
     const bool ident = h->host.C == 256;
     c.deep = !ident && h->host.deep_k > 0 ? 1 : 0;
     const uint64_t limit = (uint64_t)smem_limit - 1024;
+    const uint64_t deep_limit = std::min<uint64_t>(limit, kCarveout196 - 1024);
     struct Pref {
         int32_t bits, tile;
     };
@@ -123,9 +137,6 @@ pm_config default_config(const pm_trie *h, int smem_limit)
             for (int32_t tile : {1024, 2048, 512, 256}) prefs.push_back({exact, tile});
         for (const Pref &pf : prefs) {
             for (int32_t threads : kThreadChoices) {
-                // byte classes behind a deep level measured fastest with 31
-                // warps, not 32 (ACGT, 1 GiB: 2.98 vs 3.25 ms)
-                if (c.deep && threads > 992) continue;
                 for (int32_t pos : {8, 4}) {
                     if (ident ? !have_filter(h, k, pf.bits) : pf.bits != 8) continue;
                     if (pf.tile % (32 * pos) != 0) continue;
@@ -134,7 +145,7 @@ pm_config default_config(const pm_trie *h, int smem_limit)
                     c.filter_bits = pf.bits;
                     c.positions = pos;
                     if (!window_fits(h, c)) continue;
-                    if (pm::scan_smem_bytes(h->dev, c) <= limit) return c;
+                    if (pm::scan_smem_bytes(h->dev, c) <= (c.deep ? deep_limit : limit)) return c;
                 }
             }
         }
@@ -145,6 +156,7 @@ pm_config default_config(const pm_trie *h, int smem_limit)
     c.tile = 128;
     c.positions = 4;
     c.light_max = kLightMax;
+    c.schedule = PM_SCHED_AUTO;
     return c;
 }
 
@@ -198,6 +210,10 @@ int validate_config(const pm_trie *h, const pm_config &c, std::string &why)
     }
     if (c.light_max < 0) {
         why = "light_max must be >= 0";
+        return PM_ERR_INVAL;
+    }
+    if (c.schedule < PM_SCHED_AUTO || c.schedule > PM_SCHED_DYNAMIC) {
+        why = "schedule must be PM_SCHED_AUTO, PM_SCHED_STATIC or PM_SCHED_DYNAMIC";
         return PM_ERR_INVAL;
     }
     if (!window_fits(h, c)) {

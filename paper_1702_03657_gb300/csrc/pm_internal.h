@@ -249,6 +249,7 @@ int launch_scan(const TrieDev &t, const pm_config &cfg, const ScanArgs &a,
 // offsets), and the neighbour chunks a lane's window takes (byte classes).
 struct ScanLayout {
     uint32_t off_lut, off_warp, warp_bytes, off_queue, off_stages, stage_bytes, total;
+    uint32_t off_sched;  // dynamic schedule: the CTA's ticket counter and run ring
     uint32_t filt_u4, filt_words, halo, nnb;
 };
 ScanLayout scan_layout(const TrieDev &t, const pm_config &cfg);

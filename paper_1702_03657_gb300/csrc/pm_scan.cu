@@ -64,6 +64,7 @@ constexpr uint32_t kFull = 0xffffffffu;
 constexpr int kMaxNeighbours = 8;                  // byte classes: chunks a window takes
 constexpr uint32_t kStagePad = 16;                 // bytes past tile + halo a lane may read
 constexpr uint32_t kWarpHeader = 32;               // mbarriers of a warp's block
+constexpr uint32_t kChunkRing = 16;                // run starts a CTA keeps published
 
 enum Mode { MODE_FAST = 0, MODE_CHECKED = 1, MODE_LOOKUPS = 2 };
 
@@ -87,6 +88,7 @@ struct KParams {
     unsigned long long *lookups;
     uint32_t *tile_counts;      // single text, optional: matches per position tile
     unsigned long long *walks;  // optional: walks run
+    unsigned int *chunk_ctr;    // dynamic schedule: runs of tiles handed out (zeroed), or null
     const uint32_t *filter;     // source of the shared-memory filter (or null)
     const uint2 *dense;         // byte alphabet: dense table of level k (global)
     uint32_t first_k;           // byte alphabet: BFS id of the first depth-k node
@@ -108,6 +110,7 @@ struct KParams {
     uint32_t light_add;         // light form, one CTA: add to the count, not overwrite
     // shared-memory layout (byte offsets)
     uint32_t off_lut, off_warp;   // class table, then the per-warp blocks
+    uint32_t off_sched;           // after the warp blocks: ticket counter, run ring
     uint32_t warp_bytes;          // bytes of one warp's block
     uint32_t off_queue;           // inside a warp's block (after its mbarriers)
     uint32_t off_stages;          // inside a warp's block (after its queue)
@@ -611,6 +614,19 @@ __global__ void __launch_bounds__(1024, 1) pfac_scan_kernel(const KParams p)
 
     uint32_t *s_filt = reinterpret_cast<uint32_t *>(smem);
     uint32_t *s_lut = reinterpret_cast<uint32_t *>(smem + p.off_lut);
+    // dynamic schedule: the CTA's tickets (one per tile a warp takes) and the
+    // global runs of its local runs m, published as {m, run} in slot m % ring
+    unsigned long long *s_run = reinterpret_cast<unsigned long long *>(smem + p.off_sched);
+    unsigned int &s_tick = *reinterpret_cast<unsigned int *>(smem + p.off_sched + 8 * kChunkRing);
+    if (p.chunk_ctr != nullptr && tid == 0) {
+        s_tick = 0;
+        // local runs 0 and 1 now, in order; the other slots read as not yet
+        // published (their m is behind any run asked for)
+        s_run[0] = atomicAdd(p.chunk_ctr, 1u);
+        s_run[1] = (1ull << 32) | atomicAdd(p.chunk_ctr, 1u);
+        for (uint32_t i = 2; i < kChunkRing; ++i)
+            s_run[i] = (unsigned long long)(i - kChunkRing) << 32;
+    }
     {
         const uint4 *src = reinterpret_cast<const uint4 *>(p.filter);
         uint4 *dst = reinterpret_cast<uint4 *>(s_filt);
@@ -632,10 +648,59 @@ __global__ void __launch_bounds__(1024, 1) pfac_scan_kernel(const KParams p)
     unsigned long long look = 0;   // lookups (MODE_LOOKUPS)
     unsigned long long nwalk = 0;  // walks run
     const unsigned long long gw = (unsigned long long)blockIdx.x * NW + warp;
-    const unsigned long long TW = (unsigned long long)gridDim.x * NW;
-    const unsigned long long my_tiles = gw < ntiles ? (ntiles - 1 - gw) / TW + 1 : 0;
+    // The warp's next tile (lane 0; start byte, kNoTile past the last, or
+    // kFailTile when a bounded wait ran out). Static: tiles gw, gw + W, ... (W
+    // warps in the grid).
+    // Dynamic: ticket j of the CTA is tile j % PM_CHUNK_TILES of the CTA's
+    // local run j / PM_CHUNK_TILES. The taker of a run's first ticket asks
+    // the global counter for the run two ahead, once the run one ahead is
+    // published: global runs then grow with m, so past the first missing
+    // tile every later ticket misses too, and a warp stops at its first.
+    // (what grab needs is re-read from the parameters at each call, so that
+    // no more than the static cursor stays live across the tile loop)
+    constexpr unsigned long long kNoTile = ~0ull, kFailTile = ~1ull;
+    unsigned long long st_next = gw * p.tile;  // static: start of the warp's next tile
+    auto run_of = [&](uint32_t m, unsigned long long &run) -> bool {
+        const volatile unsigned long long *slot = s_run + m % kChunkRing;
+        unsigned long long e = *slot;
+        if ((uint32_t)(e >> 32) == m) {  // published (the usual case)
+            run = (uint32_t)e;
+            return true;
+        }
+        const long long t_end = clock64() + p.wait_budget;
+        for (;;) {
+            const int d = (int)((uint32_t)(e >> 32) - m);
+            if (d == 0) {
+                run = (uint32_t)e;
+                return true;
+            }
+            if (d > 0 || clock64() > t_end) return false;  // overwritten / ran out
+            __nanosleep(64);
+            e = *slot;
+        }
+    };
+    auto grab = [&]() -> unsigned long long {
+        const unsigned long long tot = BATCH ? __ldg(p.offsets + p.ntexts) : p.total;
+        if (p.chunk_ctr == nullptr) {
+            const unsigned long long ts = st_next;
+            st_next += (unsigned long long)gridDim.x * (blockDim.x >> 5) * p.tile;
+            return ts < tot ? ts : kNoTile;
+        }
+        const uint32_t j = atomicAdd(&s_tick, 1u);
+        const uint32_t m = j / PM_CHUNK_TILES, o = j % PM_CHUNK_TILES;
+        unsigned long long run;
+        if (o == 0) {
+            if (!run_of(m + 1, run)) return kFailTile;
+            const uint32_t g = atomicAdd(p.chunk_ctr, 1u);
+            *(volatile unsigned long long *)(s_run + (m + 2) % kChunkRing) =
+                ((unsigned long long)(m + 2) << 32) | g;
+        }
+        if (!run_of(m, run)) return kFailTile;
+        const unsigned long long ts = (run * PM_CHUNK_TILES + o) * p.tile;
+        return ts < tot ? ts : kNoTile;
+    };
 
-    if (my_tiles) {
+    {
         uint8_t *wsm = smem + p.off_warp + (size_t)warp * p.warp_bytes;
         uint64_t *bars = reinterpret_cast<uint64_t *>(wsm);
         unsigned long long *qpos = reinterpret_cast<unsigned long long *>(wsm + p.off_queue);
@@ -655,15 +720,32 @@ __global__ void __launch_bounds__(1024, 1) pfac_scan_kernel(const KParams p)
             __syncwarp();
         };
 
-        const unsigned long long tstride = TW * p.tile;  // text between a warp's tiles
+        bool failed = false;
+        // start byte of stage s's tile, held by lane s (kNoTile: none); a
+        // register, not shared memory (the shared bytes per CTA decide the
+        // L1 the SM keeps beside them)
+        unsigned long long my_ts = kNoTile;
+        // (whole warp) lane 0 takes the next tile into stage s and starts its
+        // copy; lane s keeps the tile's start
+        auto refill = [&](uint32_t s) {
+            unsigned long long ts = kNoTile;
+            if (lane == 0) {
+                ts = grab();
+                if (ts == kFailTile) {
+                    record_error(PM_ERR_TIMEOUT);
+                    ts = kNoTile;
+                }
+                if (ts != kNoTile) issue_tile(p, stages, bars, s, ts, end);
+            }
+            ts = __shfl_sync(kFull, ts, 0);
+            if (lane == s) my_ts = ts;
+        };
         if (lane == 0) {
             for (uint32_t s = 0; s < p.stages; ++s) mbar_init(&bars[s], 1);
             fence_mbar_init();
-            const unsigned long long pre = my_tiles < p.stages ? my_tiles : p.stages;
-            for (unsigned long long i = 0; i < pre; ++i)
-                issue_tile(p, stages, bars, (uint32_t)i, (gw + i * TW) * p.tile, end);
         }
-        __syncwarp();
+        __syncwarp();  // the initialised barriers, before any lane tests them
+        for (uint32_t s = 0; s < p.stages; ++s) refill(s);
 
         const uint32_t lw = p.lw;
         // byte alphabet, exact levels: filter bit index = low 8k+lw bits of
@@ -678,24 +760,27 @@ __global__ void __launch_bounds__(1024, 1) pfac_scan_kernel(const KParams p)
         const bool sw = FIXED && t.sw_shift != kNoSwar;
         const uint32_t shF = 32u - cb * Fv, shD = 32u - cb * Dv;  // used only when F, D > 0
         const uint32_t span = (p.gram > 1 ? p.gram : 1u) - 1u;  // bytes a position's filter reads past it
-        bool failed = false;
 
-        uint32_t s = 0, phase = 0;            // stage and its mbarrier phase
-        unsigned long long t0 = gw * p.tile;  // start of the current tile
-        const unsigned long long ahead = (unsigned long long)p.stages * tstride;
-        for (unsigned long long it = 0; it < my_tiles && !failed; ++it, t0 += tstride) {
+        // the stages hold the warp's tiles in the order taken; the first
+        // stage without one ends the warp's work
+        uint32_t s = 0, phase = 0;  // stage and its mbarrier phase
+        while (!failed) {
+            const unsigned long long t0 = __shfl_sync(kFull, my_ts, s);  // the current tile
+            if (t0 == kNoTile) break;
             const uint32_t nbytes = (uint32_t)tile_bytes(p, t0, end);
             uint8_t *st = stages + (size_t)s * p.stage_bytes;
 
             const bool ok = __all_sync(kFull, mbar_wait_bounded(&bars[s], phase, p.wait_budget));
             if (!ok) {
+                // copies still in flight: every stage holding a tile
+                const uint32_t held = __ballot_sync(kFull, lane < p.stages && my_ts != kNoTile);
                 if (lane == 0) {
                     record_error(PM_ERR_TIMEOUT);
-                    // copies still in flight: tiles it .. it+stages-1 (full budget)
-                    for (unsigned long long j = 0; j < p.stages && it + j < my_tiles; ++j) {
-                        const uint32_t sj = (uint32_t)((s + j) % p.stages);
-                        mbar_wait_bounded(&bars[sj], phase ^ (uint32_t)((s + j) >= p.stages),
-                                          kWaitBudget);
+                    for (uint32_t j = 0; j < p.stages; ++j) {  // (full budget)
+                        const uint32_t sj = (s + j) % p.stages;
+                        if ((held >> sj) & 1u)
+                            mbar_wait_bounded(&bars[sj], phase ^ (uint32_t)((s + j) >= p.stages),
+                                              kWaitBudget);
                     }
                 }
                 failed = true;
@@ -1097,10 +1182,8 @@ __global__ void __launch_bounds__(1024, 1) pfac_scan_kernel(const KParams p)
             }
 
             __syncwarp();  // stage s fully consumed by this warp
-            if (lane == 0 && it + p.stages < my_tiles) {
-                fence_proxy_async();
-                issue_tile(p, stages, bars, s, t0 + ahead, end);
-            }
+            if (lane == 0) fence_proxy_async();
+            refill(s);
             if (++s == p.stages) {
                 s = 0;
                 phase ^= 1u;
@@ -1367,7 +1450,8 @@ ScanLayout scan_layout(const TrieDev &t, const pm_config &cfg)
     L.off_queue = kWarpHeader;
     L.off_stages = kWarpHeader + kQueue * 12;
     L.warp_bytes = L.off_stages + (uint32_t)cfg.stages * L.stage_bytes;
-    L.total = off + (uint32_t)(cfg.threads / 32) * L.warp_bytes;
+    L.off_sched = off + (uint32_t)(cfg.threads / 32) * L.warp_bytes;
+    L.total = L.off_sched + 8 * kChunkRing + 16;
     // byte classes: neighbour chunks a lane's window needs
     uint32_t dmax = k;
     if (!ident && cfg.deep && t.deep_k > dmax) dmax = t.deep_k;
@@ -1395,6 +1479,58 @@ struct LaunchKey {
 std::map<LaunchKey, int> g_occ;  // guarded by g_attr_mu
 // largest dynamic shared memory set per (kernel, device); only ever raised
 std::map<std::pair<const void *, int>, uint32_t> g_smem_set;  // guarded by g_attr_mu
+
+// Stream-ordered pool per device for the dynamic schedule's run counters
+// (4 bytes a launch); freed blocks stay in the pool for the next launch.
+std::mutex g_pool_mu;
+std::map<int, cudaMemPool_t> g_pools;  // guarded by g_pool_mu
+
+bool run_pool(int dev, cudaMemPool_t &pool)
+{
+    std::lock_guard<std::mutex> g(g_pool_mu);
+    auto it = g_pools.find(dev);
+    if (it != g_pools.end()) {
+        pool = it->second;
+        return true;
+    }
+    cudaMemPoolProps props{};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.handleTypes = cudaMemHandleTypeNone;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    if (cudaMemPoolCreate(&pool, &props) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    uint64_t keep = ~0ull;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    g_pools.emplace(dev, pool);
+    return true;
+}
+
+// A zeroed run counter for one launch on st, or null (static schedule):
+// never while st is being captured into a graph.
+unsigned int *run_counter(int dev, cudaStream_t st)
+{
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    cudaMemPool_t pool;
+    if (cs != cudaStreamCaptureStatusNone || !run_pool(dev, pool)) return nullptr;
+    void *ctr = nullptr;
+    if (cudaMallocFromPoolAsync(&ctr, sizeof(unsigned int), pool, st) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    if (cudaMemsetAsync(ctr, 0, sizeof(unsigned int), st) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFreeAsync(ctr, st);
+        return nullptr;
+    }
+    return static_cast<unsigned int *>(ctr);
+}
 
 }  // namespace
 
@@ -1479,6 +1615,7 @@ int launch_scan(const TrieDev &t, const pm_config &cfg, const ScanArgs &a, void 
     p.warp_bytes = L.warp_bytes;
     p.off_queue = L.off_queue;
     p.off_stages = L.off_stages;
+    p.off_sched = L.off_sched;
     p.stage_bytes = L.stage_bytes;
     p.filt_u4 = L.filt_u4;
     p.filt_words = L.filt_words;
@@ -1499,10 +1636,10 @@ int launch_scan(const TrieDev &t, const pm_config &cfg, const ScanArgs &a, void 
         return PM_OK;
     }
     int occ = 0;
+    int dev = -1;
     {
         // the shared-memory attribute and the occupancy of each (kernel,
         // shared bytes, threads, device) are set and queried once
-        int dev = -1;
         e = cudaGetDevice(&dev);
         if (e != cudaSuccess) {
             msg = std::string("cudaGetDevice: ") + cudaGetErrorString(e);
@@ -1545,8 +1682,11 @@ int launch_scan(const TrieDev &t, const pm_config &cfg, const ScanArgs &a, void 
         const unsigned long long need = (ntiles + warps - 1) / warps;
         if (need < grid) grid = need;
     }
+    // the dynamic schedule's run counter (none: the static schedule)
+    p.chunk_ctr = c.schedule == PM_SCHED_DYNAMIC ? run_counter(dev, st) : nullptr;
     fn<<<(unsigned)grid, c.threads, L.total, st>>>(p);
     e = cudaGetLastError();
+    if (p.chunk_ctr) cudaFreeAsync(p.chunk_ctr, st);
     if (e != cudaSuccess) {
         msg = std::string("scan launch: ") + cudaGetErrorString(e);
         return PM_ERR_CUDA;

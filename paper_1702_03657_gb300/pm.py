@@ -27,6 +27,10 @@ PM_ERR_NOT_FOUND = -9
 PM_ERR_HOST_ONLY = -10
 PM_MAX_PATTERN_LEN = 4096
 PM_STATIC_MAX_LEN = 1 << 20
+PM_SCHED_AUTO = 0
+PM_SCHED_STATIC = 1
+PM_SCHED_DYNAMIC = 2
+PM_CHUNK_TILES = 32
 
 # every symbol include/pm.h declares (checked by the tests)
 EXPORTS = (
@@ -86,7 +90,7 @@ class pm_config(C.Structure):
     _fields_ = [(f, C.c_int32) for f in (
         "threads", "tile", "dense_k", "filter_bits", "row_search",
         "ctas_per_sm", "stages", "checked", "positions", "deep", "layout",
-        "wait_clocks", "light_max")]
+        "wait_clocks", "light_max", "schedule")]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

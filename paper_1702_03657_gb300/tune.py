@@ -39,7 +39,8 @@ def candidates(trie: pm.Trie, total_bytes: int, single: bool = False) -> List[di
             threads, tiles, (2, 3), ks, widths, (4, 8), (0, 1), lights):
         c = dict(base, threads=th, tile=tile, stages=stages, dense_k=k, filter_bits=bits,
                  positions=pos, row_search=rs, checked=0, ctas_per_sm=0, layout=0,
-                 wait_clocks=0, light_max=lm, deep=0 if ident else (1 if st["deep_k"] else 0))
+                 wait_clocks=0, light_max=lm, schedule=0,
+                 deep=0 if ident else (1 if st["deep_k"] else 0))
         key = tuple(sorted(c.items()))
         if key in seen:
             continue

@@ -172,7 +172,7 @@ def test_config_validation(lib):
     for bad in ({"threads": 100}, {"threads": 1056}, {"tile": 1000}, {"dense_k": -1},
                 {"stages": 9}, {"dense_k": 99}, {"filter_bits": 16}, {"deep": 2},
                 {"positions": 5}, {"positions": 8, "tile": 128}, {"wait_clocks": -1},
-                {"light_max": -1}):
+                {"light_max": -1}, {"schedule": 3}, {"schedule": -1}):
         c = dict(cfg, **bad)
         with pytest.raises(pm.PMError) as e:
             pm.pm_set_config(t, c)

@@ -293,7 +293,7 @@ def test_four_letter_alphabets(letters):
     o_ids, o_cnt, _ = ot.scan(text)
     assert o_cnt > 0
     for c in (None, persistent(t), persistent(t, positions=4), dict(cfg, checked=1),
-              small_cfg(t, dense_k=10), light(t)):
+              small_cfg(t, dense_k=10), light(t), persistent(t, schedule=pm.PM_SCHED_DYNAMIC)):
         ids, cnt, _ = gpu_scan(t, text, cfg=c)
         assert_same(ids, cnt, o_ids, o_cnt)
     pieces, a = [], 0
@@ -304,6 +304,39 @@ def test_four_letter_alphabets(letters):
     bw = W.Workload("four_batch", 31, pats, data, off)
     b_ids, b_counts, _ = ot.scan_batch(data, off)
     for c in (None, small_cfg(t, dense_k=10)):
+        ids, counts = batch_gpu(t, bw, c)
+        assert np.array_equal(ids, b_ids) and np.array_equal(counts, b_counts)
+
+
+@pytest.mark.parametrize("sched", [1, 2])
+def test_schedules(sched):
+    """Static schedule (warp w: tiles w, w + W, ...) and dynamic schedule
+    (CTAs take runs of PM_CHUNK_TILES tiles from a global counter, warps take
+    the run's tiles as they finish one) give the oracle's bits: texts ending
+    inside the first tile, on a run's end, one byte past it and in a partial
+    last run; 31-warp CTAs (runs not a multiple of the warps), 256-byte
+    tiles, three stages; and a batch."""
+    assert pm.PM_CHUNK_TILES == 32 and sched in (pm.PM_SCHED_STATIC, pm.PM_SCHED_DYNAMIC)
+    wl = W.paper_scale(7, text_bytes=3 * W.MiB + 13, n_patterns=3000)
+    t = pm.pm_build(wl.patterns)
+    ot = oracle.Trie(wl.patterns)
+    cfgs = (persistent(t, schedule=sched), persistent(t, schedule=sched, tile=256, threads=992),
+            small_cfg(t, schedule=sched),
+            persistent(t, schedule=sched, stages=3, positions=4, threads=512))
+    for n in (1, 255, 32 * 1024, 32 * 1024 + 1, 5 * 32 * 1024 + 7, len(wl.text)):
+        text = wl.text[:n]
+        o_ids, o_cnt, _ = ot.scan(text, threads=HOST_THREADS)
+        for c in cfgs:
+            ids, cnt, _ = gpu_scan(t, text, cfg=c)
+            assert_same(ids, cnt, o_ids, o_cnt)
+    pieces, a = [], 0
+    for n in [0, 5, 40_000, 70_000, 1, 300_000, 33 * 1024, 17]:
+        pieces.append(wl.text[a:a + n])
+        a += n + 3
+    data, off = W.concat(pieces)
+    bw = W.Workload("sched_batch", 7, wl.patterns, data, off)
+    b_ids, b_counts, _ = ot.scan_batch(data, off)
+    for c in cfgs[:2]:
         ids, counts = batch_gpu(t, bw, c)
         assert np.array_equal(ids, b_ids) and np.array_equal(counts, b_counts)
 

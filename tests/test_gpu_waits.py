@@ -3,7 +3,9 @@ bounded (pm_config.wait_clocks SM clocks; default about 2 s). With a budget
 far below a copy's latency the waits run out: the kernel records
 PM_ERR_TIMEOUT in its device error word, waits (with the full budget) for
 its copies in flight, and returns; nothing traps, the context stays usable,
-and the next scan with the default budget is bit-exact."""
+and the next scan with the default budget is bit-exact. Before each
+short-budget scan a write larger than L2 evicts the text, so that the
+first copies come from HBM."""
 import numpy as np
 import pytest
 
@@ -26,7 +28,10 @@ def _lib():
     yield
 
 
-def test_wait_that_runs_out_reports_timeout():
+@pytest.mark.parametrize("sched", [1, 2])
+def test_wait_that_runs_out_reports_timeout(sched):
+    """Both schedules; the dynamic one also waits (bounded by the same
+    budget) for its CTA's next run of tiles to be published."""
     wl = W.paper_scale(6, text_bytes=16 * W.MiB + 3, n_patterns=3000)
     t = pm.pm_build(wl.patterns)
     cfg = pm.pm_get_config(t)
@@ -35,13 +40,17 @@ def test_wait_that_runs_out_reports_timeout():
     cnt = torch.empty(1, dtype=torch.int64, device="cuda")
     torch.cuda.synchronize()
     assert pm.pm_device_error() == pm.PM_OK
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     for budget in (1, 64):
-        pm.pm_scan_ex(t, tv, None, ids, cnt, cfg=dict(cfg, wait_clocks=budget))
+        # the text out of L2 (a write larger than L2 in between), so that the
+        # first tile's copy comes from HBM, far later than the budget allows
+        flush.fill_(budget)
+        pm.pm_scan_ex(t, tv, None, ids, cnt, cfg=dict(cfg, wait_clocks=budget, schedule=sched))
         torch.cuda.synchronize()                      # the launch returned
         assert pm.pm_device_error() == pm.PM_ERR_TIMEOUT
         assert pm.pm_device_error() == pm.PM_OK       # read and cleared
     # the context is usable and the default budget gives the oracle's bits
-    pm.pm_scan(t, tv, ids, cnt)
+    pm.pm_scan_ex(t, tv, None, ids, cnt, cfg=dict(cfg, schedule=sched))
     torch.cuda.synchronize()
     assert pm.pm_device_error() == pm.PM_OK
     o_ids, o_cnt, _ = oracle.Trie(wl.patterns).scan(wl.text, threads=8)
