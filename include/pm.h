@@ -249,7 +249,8 @@ typedef struct {
 } pm_match;
 
 /* Bytes of device workspace pm_scan_all needs for a text of len bytes
- * (a match count per 1024 positions plus two per 1 Mi positions). */
+ * (a match count per 1024 positions, a bit per position, plus two counts
+ * per 1 Mi positions). */
 uint64_t pm_scan_all_work_bytes(uint64_t len);
 
 /* pm_scan_all: pm_scan of one device text (out.ids and *out.count as

@@ -404,7 +404,8 @@ int build_common(const uint8_t *const *patterns, const uint32_t *lengths, uint32
 int scan_common(const pm_trie *h, const uint8_t *d_texts, const uint64_t *d_offsets,
                 uint32_t ntexts, uint64_t len, uint64_t limit, int32_t *d_ids, int64_t *d_counts,
                 uint64_t *d_lookups, const pm_config *cfg, pm_stream stream,
-                uint32_t *tile_counts = nullptr, uint64_t *d_walks = nullptr)
+                uint32_t *tile_counts = nullptr, uint64_t *d_walks = nullptr,
+                uint32_t *match_bits = nullptr)
 {
     if (!h) return fail(PM_ERR_INVAL, "handle is NULL");
     if (!h->d_arena) return fail(PM_ERR_HOST_ONLY, "handle was built with pm_build_host");
@@ -433,6 +434,7 @@ int scan_common(const pm_trie *h, const uint8_t *d_texts, const uint64_t *d_offs
     a.counts = d_counts;
     a.lookups = reinterpret_cast<unsigned long long *>(d_lookups);
     a.tile_counts = tile_counts;
+    a.match_bits = match_bits;
     a.walks = reinterpret_cast<unsigned long long *>(d_walks);
     std::string msg;
     int rc = pm::launch_scan(h->dev, c, a, stream, h->sms, msg);
@@ -489,13 +491,15 @@ int scan_all_common(const pm_trie *h, const uint8_t *d_text, uint64_t len, uint6
                     void *d_work, pm_stream stream, uint64_t pos_base)
 {
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-    const uint64_t ntiles = (len + (1ull << pm::kMatchTileShift) - 1) >> pm::kMatchTileShift;
+    const pm::MatchWork W = pm::match_work_layout(len);
     if (len > 0) {
-        cudaError_t e = cudaMemsetAsync(d_work, 0, 4 * ntiles, st);
+        cudaError_t e = cudaMemsetAsync(d_work, 0, W.zero_bytes, st);
         if (e != cudaSuccess) return cuda_fail("cudaMemsetAsync", e);
     }
+    uint8_t *w = static_cast<uint8_t *>(d_work);
     int rc = scan_common(h, d_text, nullptr, 1, len, limit, d_ids, d_count, nullptr, nullptr,
-                         stream, len > 0 ? static_cast<uint32_t *>(d_work) : nullptr);
+                         stream, len > 0 ? reinterpret_cast<uint32_t *>(w) : nullptr, nullptr,
+                         len > 0 ? reinterpret_cast<uint32_t *>(w + W.bits) : nullptr);
     if (rc != PM_OK || len == 0) return rc;
     std::string msg;
     rc = pm::launch_matches(h->dev, d_ids, len, d_work, d_matches, capacity, stream, msg, pos_base);

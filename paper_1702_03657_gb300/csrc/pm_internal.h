@@ -225,6 +225,9 @@ struct ScanArgs {
     // single text only, optional: matches per tile of 2^kMatchTileShift
     // start positions, added to (zeroed by the caller)
     uint32_t *tile_counts;
+    // with tile_counts: one bit per start position, set where a pattern
+    // occurs (zeroed by the caller)
+    uint32_t *match_bits;
     // add to the counts instead of overwriting them
     bool keep_counts;
     // optional: number of walks queued (positions the filter, dense and deep
@@ -232,10 +235,19 @@ struct ScanArgs {
     unsigned long long *walks;
 };
 
-// All-matches listing after a single-text scan with tile_counts (same
-// stream): lists every occurrence into out[0 .. capacity) in position order,
-// longest pattern first, positions offset by pos_base. work: the tile counts
-// then the block sums and offsets (match_work_bytes(len) bytes).
+// All-matches listing after a single-text scan with tile_counts and
+// match_bits (same stream): lists every occurrence into out[0 .. capacity)
+// in position order, longest pattern first, positions offset by pos_base.
+// work (match_work_bytes(len) bytes): the tile counts and the match bits
+// (both zeroed before the scan, zero_bytes from the start), then the block
+// sums and offsets.
+struct MatchWork {
+    uint64_t bits;        // byte offset of the match bits
+    uint64_t bsum, boff;  // byte offsets of the block sums and offsets
+    uint64_t zero_bytes;  // bytes to zero before the scan
+    uint64_t total;
+};
+MatchWork match_work_layout(uint64_t len);
 uint64_t match_work_bytes(uint64_t len);
 int launch_matches(const TrieDev &t, const int32_t *ids, uint64_t len, void *work,
                    pm_match *out, uint64_t capacity, void *stream, std::string &msg,

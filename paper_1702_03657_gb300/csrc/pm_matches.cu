@@ -1,15 +1,17 @@
 // All-matches listing (Sections II-B and II-C ask for every occurrence of
 // every pattern): after a single-text scan has written the longest-match id
 // of every position and, per tile of 2^kMatchTileShift positions, the
-// number of occurrences starting there, three kernels list every occurrence
-// in position order, longest pattern first at a position:
+// number of occurrences starting there and a bit per position that holds
+// one, three kernels list every occurrence in position order, longest
+// pattern first at a position:
 //   1. the match count of each block of kTilesPerBlock tiles;
 //   2. an exclusive scan of those block sums (one CTA);
 //   3. per block, an exclusive scan of its tile counts gives each tile's
-//      first output slot; warps take the tiles with matches, read their ids,
-//      and expand each matched position into the chain of patterns on its
-//      walk (the longest first, each pattern's next shorter one from the
-//      per-id table), at offsets from a warp scan.
+//      first output slot; warps take the tiles with matches, read the ids of
+//      the positions marked in the match bits (not the whole id array), and
+//      expand each into the chain of patterns on its walk (the longest
+//      first, each pattern's next shorter one from the per-id table), at
+//      offsets from a warp scan.
 // The patterns occurring at a position are exactly the prefixes of its
 // longest match that are patterns, so the ids and the chains determine the
 // whole list.
@@ -89,11 +91,11 @@ __global__ void __launch_bounds__(1024, 1) pm_block_scan_kernel(const unsigned l
 
 // One block of kTilesPerBlock tiles, one tile per thread for the scan of
 // the tile counts; then each warp lists its tiles with matches, each lane
-// 32 consecutive positions of the tile (read with 16-byte loads when the
-// ids are aligned), ordered across lanes by one warp scan of their record
-// counts.
+// 32 consecutive positions of the tile: one word of the match bits says
+// which of them hold a match, and only their ids are read. Lanes are
+// ordered by one warp scan of their record counts.
 __global__ void __launch_bounds__(1024, 1) pm_matches_write_kernel(
-    const int32_t *ids, uint64_t len, const uint32_t *tc, uint64_t ntiles,
+    const int32_t *ids, const uint32_t *bits, uint64_t len, const uint32_t *tc, uint64_t ntiles,
     const unsigned long long *boff, const int4 *minfo, pm_match *out, uint64_t cap,
     uint64_t pos_base)
 {
@@ -110,37 +112,21 @@ __global__ void __launch_bounds__(1024, 1) pm_matches_write_kernel(
         toff[threadIdx.x] = boff[blockIdx.x] + block_exclusive_scan(c, ws, &tot);
     }
     __syncthreads();
-    const bool vec = ((uintptr_t)ids & 15u) == 0;
     for (uint32_t i = warp; i < kTilesPerBlock; i += 32) {
         if (tcs[i] == 0) continue;
         const uint64_t q0 = ((b0 + i) << kMatchTileShift) + 32ull * lane;  // lane's positions
-        int32_t v[32];
-        if (vec && q0 + 32 <= len) {
-            const int4 *src = reinterpret_cast<const int4 *>(ids + q0);
-#pragma unroll
-            for (int r = 0; r < 8; ++r) {
-                const int4 x = __ldg(src + r);
-                v[4 * r] = x.x;
-                v[4 * r + 1] = x.y;
-                v[4 * r + 2] = x.z;
-                v[4 * r + 3] = x.w;
-            }
-        } else {
-#pragma unroll
-            for (int r = 0; r < 32; ++r) v[r] = q0 + r < len ? __ldg(ids + q0 + r) : -1;
-        }
+        // bit r: position q0 + r holds a match (only positions below len do)
+        const uint32_t mask = q0 < len ? __ldg(bits + (q0 >> 5)) : 0u;
         unsigned long long m = 0;
-#pragma unroll
-        for (int r = 0; r < 32; ++r)
-            if (v[r] >= 0) m += (unsigned long long)__ldg(&minfo[v[r]].z);
+        for (uint32_t w = mask; w; w &= w - 1)
+            m += (unsigned long long)__ldg(&minfo[__ldg(ids + q0 + __ffs(w) - 1)].z);
         const unsigned long long x = warp_inclusive_scan(m, lane);
         unsigned long long slot = toff[i] + x - m;
         if (m == 0) continue;
-#pragma unroll
-        for (int r = 0; r < 32; ++r) {
-            if (v[r] < 0) continue;
+        for (uint32_t w = mask; w; w &= w - 1) {
+            const uint32_t r = __ffs(w) - 1;
             // the position's patterns, longest first, down the chain
-            int32_t q = v[r];
+            int32_t q = __ldg(ids + q0 + r);
             int4 mi = __ldg(minfo + q);
             const int32_t cnt = mi.z;
             for (int32_t k = 0; k < cnt; ++k) {
@@ -163,12 +149,20 @@ __global__ void __launch_bounds__(1024, 1) pm_matches_write_kernel(
 
 }  // namespace
 
-uint64_t match_work_bytes(uint64_t len)
+MatchWork match_work_layout(uint64_t len)
 {
     const uint64_t ntiles = (len + (1ull << kMatchTileShift) - 1) >> kMatchTileShift;
     const uint64_t nb = (ntiles + kTilesPerBlock - 1) / kTilesPerBlock;
-    return round256(4 * ntiles) + 2 * round256(8 * nb);
+    MatchWork W{};
+    W.bits = round256(4 * ntiles);
+    W.zero_bytes = W.bits + 4 * ((len + 31) / 32);
+    W.bsum = round256(W.zero_bytes);
+    W.boff = W.bsum + round256(8 * nb);
+    W.total = W.boff + round256(8 * nb);
+    return W;
 }
+
+uint64_t match_work_bytes(uint64_t len) { return match_work_layout(len).total; }
 
 int launch_matches(const TrieDev &t, const int32_t *ids, uint64_t len, void *work,
                    pm_match *out, uint64_t capacity, void *stream, std::string &msg,
@@ -178,15 +172,16 @@ int launch_matches(const TrieDev &t, const int32_t *ids, uint64_t len, void *wor
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     const uint64_t ntiles = (len + (1ull << kMatchTileShift) - 1) >> kMatchTileShift;
     const uint64_t nb = (ntiles + kTilesPerBlock - 1) / kTilesPerBlock;
+    const MatchWork W = match_work_layout(len);
     uint8_t *w = static_cast<uint8_t *>(work);
     uint32_t *tc = reinterpret_cast<uint32_t *>(w);
-    unsigned long long *bsum = reinterpret_cast<unsigned long long *>(w + round256(4 * ntiles));
-    unsigned long long *boff =
-        reinterpret_cast<unsigned long long *>(w + round256(4 * ntiles) + round256(8 * nb));
+    const uint32_t *bits = reinterpret_cast<const uint32_t *>(w + W.bits);
+    unsigned long long *bsum = reinterpret_cast<unsigned long long *>(w + W.bsum);
+    unsigned long long *boff = reinterpret_cast<unsigned long long *>(w + W.boff);
     pm_tile_sums_kernel<<<(unsigned)nb, 1024, 0, st>>>(tc, ntiles, bsum);
     pm_block_scan_kernel<<<1, 1024, 0, st>>>(bsum, (uint32_t)nb, boff);
-    pm_matches_write_kernel<<<(unsigned)nb, 1024, 0, st>>>(ids, len, tc, ntiles, boff, t.minfo,
-                                                           out, capacity, pos_base);
+    pm_matches_write_kernel<<<(unsigned)nb, 1024, 0, st>>>(ids, bits, len, tc, ntiles, boff,
+                                                           t.minfo, out, capacity, pos_base);
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) {
         msg = std::string("all-matches launch: ") + cudaGetErrorString(e);

@@ -87,6 +87,7 @@ struct KParams {
     int64_t *counts;
     unsigned long long *lookups;
     uint32_t *tile_counts;      // single text, optional: matches per position tile
+    uint32_t *match_bits;       // with tile_counts: a bit per position with a match
     unsigned long long *walks;  // optional: walks run
     unsigned int *chunk_ctr;    // dynamic schedule: runs of tiles handed out (zeroed), or null
     const uint32_t *filter;     // source of the shared-memory filter (or null)
@@ -362,7 +363,10 @@ __device__ __forceinline__ void emit_values(const KParams &p, unsigned long long
         atomicAdd(reinterpret_cast<unsigned long long *>(p.counts + txt), (unsigned long long)em.y);
     } else {
         acc += (unsigned)em.y;
-        if (p.tile_counts) atomicAdd(p.tile_counts + (pos >> kMatchTileShift), (unsigned)em.y);
+        if (p.tile_counts) {
+            atomicAdd(p.tile_counts + (pos >> kMatchTileShift), (unsigned)em.y);
+            atomicOr(p.match_bits + (pos >> 5), 1u << (pos & 31u));
+        }
     }
 }
 
@@ -1586,6 +1590,7 @@ int launch_scan(const TrieDev &t, const pm_config &cfg, const ScanArgs &a, void 
     p.counts = a.counts;
     p.lookups = a.lookups;
     p.tile_counts = batch ? nullptr : a.tile_counts;
+    p.match_bits = batch ? nullptr : a.match_bits;
     p.walks = a.walks;
     p.tile = (uint32_t)c.tile;
     p.halo = L.halo;

@@ -186,14 +186,16 @@ def test_config_validation(lib):
 
 
 def test_scan_all_host_side(lib):
-    """Workspace sizing (one u32 per 1024 positions, 256-byte aligned, plus
-    two u64 per 1024 tiles) and the errors that need no GPU."""
+    """Workspace sizing (one u32 per 1024 positions, 256-byte aligned, and a
+    bit per position in u32 words, together 256-byte aligned, plus two u64
+    per 1024 tiles) and the errors that need no GPU."""
     def r256(x):
         return (x + 255) // 256 * 256
-    for n in (0, 1, 1024, 1025, 1024 * 1024, 1024 * 1024 + 1, 1 << 30):
+    for n in (0, 1, 31, 32, 33, 1024, 1025, 1024 * 1024, 1024 * 1024 + 1, 1 << 30):
         tiles = -(-n // 1024)
         blocks = -(-tiles // 1024)
-        assert pm.pm_scan_all_work_bytes(n) == r256(4 * tiles) + 2 * r256(8 * blocks)
+        counts_and_bits = r256(r256(4 * tiles) + 4 * -(-n // 32))
+        assert pm.pm_scan_all_work_bytes(n) == counts_and_bits + 2 * r256(8 * blocks)
     import ctypes as C
     t = pm.pm_build_host([b"abc"])
     res = pm.pm_result(None, None)
