@@ -116,6 +116,23 @@ def test_paper_scale_reduced_all():
     assert_all_same(got, exp)
 
 
+def test_acgt_reduced_all():
+    """Dense matches: 4 MiB of the ACGT workload (about one position in a
+    hundred starts a pattern, most 32-position words hold one), every record
+    against the oracle's list; then the same through pm_scan_all_host."""
+    wl = W.acgt(2, text_bytes=4 * W.MiB + 29, n_patterns=100_000)
+    t = pm.pm_build(wl.patterns)
+    exp = oracle.Trie(wl.patterns).scan_all(wl.text, threads=8)
+    assert len(exp[0]) > 20_000
+    ids, cnt, got = gpu_all(t, wl.text, capacity=len(exp[0]) + 10)
+    assert cnt == len(exp[0])
+    assert_all_same(got, exp)
+    # a capacity that cuts the list inside a dense tile
+    ids, cnt, got = gpu_all(t, wl.text, capacity=len(exp[0]) // 2 + 3)
+    assert cnt == len(exp[0])
+    assert_all_same(got, tuple(e[:len(exp[0]) // 2 + 3] for e in exp))
+
+
 def check_list_properties(pats, text, ids, cnt, got):
     pos, mid, lens = got
     assert len(pos) == cnt
