@@ -110,7 +110,8 @@ typedef struct {
     int32_t ctas_per_sm;  /* persistent grid = SMs * ctas_per_sm (0: maximum) */
     int32_t stages;       /* tiles in flight per warp (TMA), 2..4             */
     int32_t checked;      /* 1: bounds-checked scan (PM_ERR_BOUNDS on error)  */
-    int32_t positions;    /* start positions per lane and group: 4 or 8       */
+    int32_t positions;    /* start positions per lane and group: 4 or 8, or   */
+                          /* 16 for the byte alphabet at dense_k 2            */
     int32_t deep;         /* byte classes: 1: positions passing the filter    */
                           /* look up the deep level before walking, 0: they  */
                           /* walk from the root; byte alphabet: 0             */

@@ -88,8 +88,9 @@ bool window_fits(const pm_trie *h, const pm_config &c)
 }
 
 // Default launch configuration: one CTA per SM, 1 KiB tiles double-buffered
-// with as many warps as the shared memory allows, eight positions per lane
-// where the window allows, and the deepest filter level that fits. For
+// with as many warps as the shared memory allows, sixteen positions per lane
+// at the byte alphabet's Bloom level and eight elsewhere where the window
+// allows, and the deepest filter level that fits. For
 // the byte alphabet's Bloom filter the wider filter comes first (fewer
 // walks); byte-class tries look up the deep level behind their filter. An
 // autotuner may refine it.
@@ -137,7 +138,11 @@ pm_config default_config(const pm_trie *h, int smem_limit)
             for (int32_t tile : {1024, 2048, 512, 256}) prefs.push_back({exact, tile});
         for (const Pref &pf : prefs) {
             for (int32_t threads : kThreadChoices) {
-                for (int32_t pos : {8, 4}) {
+                for (int32_t pos : {16, 8, 4}) {
+                    // sixteen positions a lane: the byte alphabet's Bloom
+                    // level (paper scale, 256 MiB: 0.236 ms against 0.256
+                    // with eight)
+                    if (pos == 16 && !(ident && k == 2)) continue;
                     if (ident ? !have_filter(h, k, pf.bits) : pf.bits != 8) continue;
                     if (pf.tile % (32 * pos) != 0) continue;
                     c.threads = threads;
@@ -167,8 +172,12 @@ int validate_config(const pm_trie *h, const pm_config &c, std::string &why)
         why = "threads must be a multiple of 32 in [128, 1024]";
         return PM_ERR_INVAL;
     }
-    if (c.positions != 4 && c.positions != 8) {
-        why = "positions must be 4 or 8";
+    if (c.positions == 16 && (h->host.C != 256 || c.dense_k != 2)) {
+        why = "16 positions per lane only for the byte alphabet at dense_k 2";
+        return PM_ERR_INVAL;
+    }
+    if (c.positions != 4 && c.positions != 8 && c.positions != 16) {
+        why = "positions must be 4, 8 or 16";
         return PM_ERR_INVAL;
     }
     if (c.tile < 32 * c.positions || c.tile > 32768 || c.tile % (32 * c.positions) != 0) {

@@ -971,7 +971,7 @@ __global__ void __launch_bounds__(1024, 1) pfac_scan_kernel(const KParams p)
                         // byte classes: the F-gram at each position in the
                         // exact shared-memory bitmap
                         if (p.F == 0) {
-                            need = (1u << P) - 1u;
+                            need = (uint32_t)((1ull << P) - 1ull);
                         } else {
                             uint64_t Xq = X;
                             uint32_t acc_f = 0;
@@ -1253,6 +1253,12 @@ KernelFn pick_kernel_p(const TrieDev &t, uint32_t k, uint32_t gram, uint32_t D, 
 KernelFn pick_kernel(const TrieDev &t, uint32_t k, uint32_t gram, uint32_t D, bool batch,
                      int mode, int positions)
 {
+    // sixteen positions a lane: the byte alphabet's Bloom level only (the
+    // configuration check admits nothing else); a group is then 512
+    // positions, which halves the per-position share of the group's fixed
+    // work (its -1 rows, queue test and loop) against eight
+    if (positions == 16 && mode != MODE_LOOKUPS && t.C == 256 && k == 2)
+        return gram == 4 ? pick_mode<2, 4, true, 16>(batch, mode) : pick_mode<2, 3, true, 16>(batch, mode);
     if (positions == 8 && mode != MODE_LOOKUPS)
         return pick_kernel_p<8>(t, k, gram, D, batch, mode);
     return pick_kernel_p<4>(t, k, gram, D, batch, mode);

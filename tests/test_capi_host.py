@@ -172,7 +172,7 @@ def test_config_validation(lib):
     for bad in ({"threads": 100}, {"threads": 1056}, {"tile": 1000}, {"dense_k": -1},
                 {"stages": 9}, {"dense_k": 99}, {"filter_bits": 16}, {"deep": 2},
                 {"positions": 5}, {"positions": 8, "tile": 128}, {"wait_clocks": -1},
-                {"light_max": -1}, {"schedule": 3}, {"schedule": -1}):
+                {"light_max": -1}, {"schedule": 3}, {"schedule": -1}, {"positions": 16}):
         c = dict(cfg, **bad)
         with pytest.raises(pm.PMError) as e:
             pm.pm_set_config(t, c)
@@ -180,9 +180,13 @@ def test_config_validation(lib):
     tb = pm.pm_build_host([bytes([b, (b + 1) % 256, 7]) for b in range(256)])
     cb = pm.pm_get_config(tb)
     assert pm.pm_stats(tb)["alphabet"] == 256 and cb["deep"] == 0
-    for bad in ({"deep": 1}, {"filter_bits": 12}):
+    # sixteen positions a lane: the default at the byte alphabet's Bloom
+    # level (dense_k 2), refused at the other levels
+    assert cb["dense_k"] == 2 and cb["positions"] == 16
+    for bad in ({"deep": 1}, {"filter_bits": 12}, {"dense_k": 1}, {"positions": 16, "tile": 256}):
         with pytest.raises(pm.PMError):
             pm.pm_set_config(tb, dict(cb, **bad))
+    pm.pm_set_config(tb, dict(cb, dense_k=1, positions=8))
 
 
 def test_scan_all_host_side(lib):

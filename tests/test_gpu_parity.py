@@ -139,7 +139,7 @@ def test_config_sweep():
                                      filter_bits=bits, row_search=rs, light_max=0,
                                      stages=2 + (tile == 128) * 2,
                                      checked=int(threads == 256),
-                                     positions=(4, 8)[(rs + threads // 128) % 2])
+                                     positions=(4, 8, 16)[(rs + threads // 128 + tile // 1024) % 3])
                             try:
                                 pm.pm_set_config(t, c)
                             except pm.PMError:
@@ -337,6 +337,39 @@ def test_schedules(sched):
     bw = W.Workload("sched_batch", 7, wl.patterns, data, off)
     b_ids, b_counts, _ = ot.scan_batch(data, off)
     for c in cfgs[:2]:
+        ids, counts = batch_gpu(t, bw, c)
+        assert np.array_equal(ids, b_ids) and np.array_equal(counts, b_counts)
+
+
+def test_sixteen_positions():
+    """Sixteen positions a lane (512-position groups) at the byte alphabet's
+    Bloom level, the default there: one and two groups a tile, checked mode,
+    three stages, small CTAs, unaligned text, a text ending inside a group,
+    and a batch; every id equals the oracle's."""
+    wl = W.paper_scale(8, text_bytes=2 * W.MiB + 333, n_patterns=4000)
+    t = pm.pm_build(wl.patterns)
+    assert pm.pm_get_config(t)["positions"] == 16
+    ot = oracle.Trie(wl.patterns)
+    o_ids, o_cnt, _ = ot.scan(wl.text, threads=HOST_THREADS)
+    for c in (persistent(t), persistent(t, tile=512), persistent(t, checked=1),
+              persistent(t, stages=3, threads=512), small_cfg(t, positions=16, tile=512),
+              persistent(t, schedule=2)):
+        ids, cnt, _ = gpu_scan(t, wl.text, cfg=c)
+        assert_same(ids, cnt, o_ids, o_cnt)
+        ids, cnt, _ = gpu_scan(t, wl.text, cfg=c, offset=5)
+        assert_same(ids, cnt, o_ids, o_cnt)
+    for n in (511, 513, 100_001):
+        e_ids, e_cnt, _ = ot.scan(wl.text[:n])
+        ids, cnt, _ = gpu_scan(t, wl.text[:n], cfg=persistent(t))
+        assert_same(ids, cnt, e_ids, e_cnt)
+    pieces, a = [], 0
+    for n in [0, 7, 511, 512, 513, 40_000, 3, 200_000]:
+        pieces.append(wl.text[a:a + n])
+        a += n + 11
+    data, off = W.concat(pieces)
+    bw = W.Workload("p16_batch", 8, wl.patterns, data, off)
+    b_ids, b_counts, _ = ot.scan_batch(data, off)
+    for c in (None, persistent(t), persistent(t, checked=1)):
         ids, counts = batch_gpu(t, bw, c)
         assert np.array_equal(ids, b_ids) and np.array_equal(counts, b_counts)
 
