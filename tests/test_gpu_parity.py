@@ -320,7 +320,7 @@ def test_schedules(sched):
     wl = W.paper_scale(7, text_bytes=3 * W.MiB + 13, n_patterns=3000)
     t = pm.pm_build(wl.patterns)
     ot = oracle.Trie(wl.patterns)
-    cfgs = (persistent(t, schedule=sched), persistent(t, schedule=sched, tile=256, threads=992),
+    cfgs = (persistent(t, schedule=sched), persistent(t, schedule=sched, tile=256, threads=992, positions=8),
             small_cfg(t, schedule=sched),
             persistent(t, schedule=sched, stages=3, positions=4, threads=512))
     for n in (1, 255, 32 * 1024, 32 * 1024 + 1, 5 * 32 * 1024 + 7, len(wl.text)):
