@@ -579,6 +579,44 @@ def test_batch_graph_capture_and_streams():
     assert np.array_equal(ids2.cpu().numpy(), o2) and int(c2.item()) == oc2
 
 
+def test_dynamic_schedule_capture_and_streams():
+    """PM_SCHED_DYNAMIC asks for a run counter per launch from a stream-ordered
+    pool. Captured into a CUDA graph the launch takes the static schedule
+    instead (no allocation in the graph) and replays bit-exactly; launched on
+    two streams at once with one handle, each launch has its own counter."""
+    wl = W.paper_scale(5, text_bytes=12 * W.MiB + 1, n_patterns=3000)
+    t = pm.pm_build(wl.patterns)
+    dyn = dict(pm.pm_get_config(t), schedule=pm.PM_SCHED_DYNAMIC)
+    o_ids, o_cnt, _ = oracle.Trie(wl.patterns).scan(wl.text, threads=HOST_THREADS)
+    tx = dev(wl.text)
+    ids = torch.empty(len(wl.text), dtype=torch.int32, device="cuda")
+    cnt = torch.empty(1, dtype=torch.int64, device="cuda")
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        pm.pm_scan_ex(t, tx, None, ids, cnt, cfg=dyn)   # warm-up outside capture
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        pm.pm_scan_ex(t, tx, None, ids, cnt, cfg=dyn)
+    for _ in range(2):
+        ids.fill_(-9)
+        g.replay()
+        torch.cuda.synchronize()
+        assert_same(ids.cpu().numpy(), int(cnt.item()), o_ids, o_cnt)
+    ids2 = torch.empty_like(ids)
+    cnt2 = torch.empty_like(cnt)
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+    for _ in range(4):
+        with torch.cuda.stream(s1):
+            pm.pm_scan_ex(t, tx, None, ids, cnt, cfg=dyn)
+        with torch.cuda.stream(s2):
+            pm.pm_scan_ex(t, tx, None, ids2, cnt2, cfg=dyn)
+    torch.cuda.synchronize()
+    assert_same(ids.cpu().numpy(), int(cnt.item()), o_ids, o_cnt)
+    assert_same(ids2.cpu().numpy(), int(cnt2.item()), o_ids, o_cnt)
+    assert pm.pm_device_error() == pm.PM_OK
+
+
 def test_scan_host_chunks():
     """pm_scan_host cuts the text into chunks that overlap by max_len-1; a
     match straddling the chunk boundary must be found."""
