@@ -558,6 +558,32 @@ __device__ __forceinline__ uint32_t classify(const uint8_t *st, const uint32_t *
     return c;
 }
 
+// The P bytes at s (P-byte aligned in shared memory) as P/4 little-endian
+// words in w[0 .. P/4), read as wide as their alignment allows, and the 4
+// bytes after them in w[P/4].
+template <int P>
+__device__ __forceinline__ void load_words(const uint8_t *s, uint32_t *w)
+{
+    if constexpr (P % 16 == 0) {
+#pragma unroll
+        for (int j = 0; j < P / 16; ++j) {
+            const uint4 v = *reinterpret_cast<const uint4 *>(s + 16 * j);
+            w[4 * j] = v.x;
+            w[4 * j + 1] = v.y;
+            w[4 * j + 2] = v.z;
+            w[4 * j + 3] = v.w;
+        }
+    } else if constexpr (P == 8) {
+        const uint2 v = *reinterpret_cast<const uint2 *>(s);
+        w[0] = v.x;
+        w[1] = v.y;
+    } else {
+#pragma unroll
+        for (int j = 0; j < P / 4; ++j) w[j] = *reinterpret_cast<const uint32_t *>(s + 4 * j);
+    }
+    w[P / 4] = *reinterpret_cast<const uint32_t *>(s + P);
+}
+
 // Shifts bit 0 of r in at the top of acc: after P steps the first step's bit
 // is at bit 32 - P and the last's at bit 31, so acc >> (32 - P) has step q's
 // bit at bit q.
@@ -861,10 +887,12 @@ __global__ void __launch_bounds__(1024, 1) pfac_scan_kernel(const KParams p)
                 if (fast) {
                     if (IDENT) {
                         // bytes lp0 .. lp0 + P + 3 (staged)
+                        // (a lane's bytes start on a P-byte boundary of the
+                        // 16-byte-aligned stage: one 16- or 8-byte load per
+                        // 16 or 8 bytes, a quarter of the wavefronts of
+                        // 4-byte loads at that lane stride)
                         uint32_t w[P / 4 + 1];
-#pragma unroll
-                        for (int j = 0; j <= P / 4; ++j)
-                            w[j] = *reinterpret_cast<const uint32_t *>(st + lp0 + 4 * j);
+                        load_words<P>(st + lp0, w);
 #define PM_WIN(q) ((q) % 4 == 0 ? w[(q) / 4] : __funnelshift_r(w[(q) / 4], w[(q) / 4 + 1], 8 * ((q) % 4)))
                         if (KF >= (int)kBloomK) {
                             // blocked Bloom test of the g-gram at each position
