@@ -111,7 +111,9 @@ typedef struct {
     int32_t stages;       /* tiles in flight per warp (TMA), 2..4             */
     int32_t checked;      /* 1: bounds-checked scan (PM_ERR_BOUNDS on error)  */
     int32_t positions;    /* start positions per lane and group: 4 or 8, or   */
-                          /* 16 for the byte alphabet at dense_k 2            */
+                          /* 16 for the byte alphabet at dense_k 2 and for    */
+                          /* 2-bit classes at dense_k 10 with the deep level  */
+                          /* of depth 13                                      */
     int32_t deep;         /* byte classes: 1: positions passing the filter    */
                           /* look up the deep level before walking, 0: they  */
                           /* walk from the root; byte alphabet: 0             */

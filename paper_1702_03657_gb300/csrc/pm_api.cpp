@@ -89,8 +89,9 @@ bool window_fits(const pm_trie *h, const pm_config &c)
 
 // Default launch configuration: one CTA per SM, 1 KiB tiles double-buffered
 // with as many warps as the shared memory allows, sixteen positions per lane
-// at the byte alphabet's Bloom level and eight elsewhere where the window
-// allows, and the deepest filter level that fits. For
+// at the byte alphabet's Bloom level and for four-letter classes at the
+// fixed shapes, eight elsewhere where the window allows, and the deepest
+// filter level that fits. For
 // the byte alphabet's Bloom filter the wider filter comes first (fewer
 // walks); byte-class tries look up the deep level behind their filter. An
 // autotuner may refine it.
@@ -141,8 +142,11 @@ pm_config default_config(const pm_trie *h, int smem_limit)
                 for (int32_t pos : {16, 8, 4}) {
                     // sixteen positions a lane: the byte alphabet's Bloom
                     // level (paper scale, 256 MiB: 0.236 ms against 0.256
-                    // with eight)
-                    if (pos == 16 && !(ident && k == 2)) continue;
+                    // with eight) and the four-letter fixed shapes (ACGT,
+                    // 1 GiB: 1.987 ms against 2.094)
+                    const bool fixed16 = !ident && c.deep && h->host.cb == 2 && k == 10 &&
+                                         h->host.deep_k == 13;
+                    if (pos == 16 && !(ident && k == 2) && !fixed16) continue;
                     if (ident ? !have_filter(h, k, pf.bits) : pf.bits != 8) continue;
                     if (pf.tile % (32 * pos) != 0) continue;
                     c.threads = threads;
@@ -172,8 +176,11 @@ int validate_config(const pm_trie *h, const pm_config &c, std::string &why)
         why = "threads must be a multiple of 32 in [128, 1024]";
         return PM_ERR_INVAL;
     }
-    if (c.positions == 16 && (h->host.C != 256 || c.dense_k != 2)) {
-        why = "16 positions per lane only for the byte alphabet at dense_k 2";
+    if (c.positions == 16 &&
+        !(h->host.C == 256 && c.dense_k == 2) &&
+        !(h->host.C != 256 && h->host.cb == 2 && c.dense_k == 10 && c.deep && h->host.deep_k == 13)) {
+        why = "16 positions per lane only for the byte alphabet at dense_k 2 and for 2-bit "
+              "classes at filter depth 10 with the deep level of depth 13";
         return PM_ERR_INVAL;
     }
     if (c.positions != 4 && c.positions != 8 && c.positions != 16) {

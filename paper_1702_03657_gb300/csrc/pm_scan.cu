@@ -972,25 +972,31 @@ __global__ void __launch_bounds__(1024, 1) pfac_scan_kernel(const KParams p)
                             }
                             if (DC > FC && need) {
                                 // the D-gram's bit in the deep level (L2):
-                                // all loads issued, then tested (a position
-                                // not tested keeps word 0: bit clear)
-                                uint32_t dw[P];
-#pragma unroll
-                                for (int q = 0; q < P; ++q) {
-                                    dw[q] = 0;
-                                    if (!((need >> q) & 1u)) continue;
-                                    const uint32_t code = (uint32_t)(X >> (64 - CB * (q + DC))) & DM;
-                                    if (MODE == MODE_CHECKED && (code >> 5) >= t.deep_words) {
-                                        record_error(PM_ERR_BOUNDS);
-                                        continue;
-                                    }
-                                    dw[q] = ld_trie_u32(t.deep + (code >> 5), pol);
-                                }
+                                // eight loads issued, then tested (a position
+                                // not tested keeps word 0: bit clear); with
+                                // sixteen positions, in two halves
+                                constexpr int H = P < 8 ? P : 8;
                                 uint32_t acc_d = 0;
 #pragma unroll
-                                for (int q = 0; q < P; ++q) {
-                                    const uint32_t a = (uint32_t)(X >> (64 - CB * (q + DC)));
-                                    acc_d = funnel_in(acc_d, __funnelshift_r(dw[q], dw[q], a));
+                                for (int h0 = 0; h0 < P; h0 += H) {
+                                    uint32_t dw[H];
+#pragma unroll
+                                    for (int k = 0; k < H; ++k) {
+                                        const int q = h0 + k;
+                                        dw[k] = 0;
+                                        if (!((need >> q) & 1u)) continue;
+                                        const uint32_t code = (uint32_t)(X >> (64 - CB * (q + DC))) & DM;
+                                        if (MODE == MODE_CHECKED && (code >> 5) >= t.deep_words) {
+                                            record_error(PM_ERR_BOUNDS);
+                                            continue;
+                                        }
+                                        dw[k] = ld_trie_u32(t.deep + (code >> 5), pol);
+                                    }
+#pragma unroll
+                                    for (int k = 0; k < H; ++k) {
+                                        const uint32_t a = (uint32_t)(X >> (64 - CB * (h0 + k + DC)));
+                                        acc_d = funnel_in(acc_d, __funnelshift_r(dw[k], dw[k], a));
+                                    }
                                 }
                                 need = acc_d >> (32 - P);
                             }
@@ -1287,6 +1293,11 @@ KernelFn pick_kernel(const TrieDev &t, uint32_t k, uint32_t gram, uint32_t D, bo
     // work (its -1 rows, queue test and loop) against eight
     if (positions == 16 && mode != MODE_LOOKUPS && t.C == 256 && k == 2)
         return gram == 4 ? pick_mode<2, 4, true, 16>(batch, mode) : pick_mode<2, 3, true, 16>(batch, mode);
+    // and the four-letter fixed shapes: 16 two-bit classes and one 32-bit
+    // neighbour chunk hold the 28 classes a lane's positions and their
+    // 13-grams need
+    if (positions == 16 && mode != MODE_LOOKUPS && t.cb == 2 && k == 10 && D == 13)
+        return pick_mode<-1, 0, false, 16, 2, 10, 13>(batch, mode);
     if (positions == 8 && mode != MODE_LOOKUPS)
         return pick_kernel_p<8>(t, k, gram, D, batch, mode);
     return pick_kernel_p<4>(t, k, gram, D, batch, mode);

@@ -36,7 +36,7 @@ def candidates(trie: pm.Trie, total_bytes: int, single: bool = False) -> List[di
     lights = (0, 1 << 30) if single and total_bytes <= (1 << 20) else (0,)
     out, seen = [], set()
     for th, tile, stages, k, bits, pos, rs, lm in itertools.product(
-            threads, tiles, (2, 3), ks, widths, (4, 8, 16) if ident else (4, 8), (0, 1), lights):
+            threads, tiles, (2, 3), ks, widths, (4, 8, 16), (0, 1), lights):
         c = dict(base, threads=th, tile=tile, stages=stages, dense_k=k, filter_bits=bits,
                  positions=pos, row_search=rs, checked=0, ctas_per_sm=0, layout=0,
                  wait_clocks=0, light_max=lm, schedule=0,
