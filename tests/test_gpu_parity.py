@@ -76,6 +76,12 @@ def small_cfg(trie, **kw):
     return c
 
 
+def no_deep(cfg):
+    """cfg without the deep level: sixteen positions a lane need it (or the
+    byte alphabet), so such a configuration goes to eight."""
+    return dict(cfg, deep=0, positions=min(cfg["positions"], 8))
+
+
 def persistent(trie, **kw):
     """The handle's configuration with the light form off."""
     return dict(pm.pm_get_config(trie), light_max=0, **kw)
@@ -222,7 +228,7 @@ def test_deep_level(seed, alphabet, npat, lo, hi, deep_k):
     ot = oracle.Trie(wl.patterns)
     o_ids, o_cnt, o_look = ot.scan(text)
     assert o_cnt > 0
-    for c in (None, dict(cfg, deep=0), dict(cfg, checked=1), small_cfg(t),
+    for c in (None, no_deep(cfg), dict(cfg, checked=1), small_cfg(t),
               small_cfg(t, deep=0, dense_k=1), dict(cfg, tile=128, stages=4, positions=4),
               dict(cfg, positions=4), small_cfg(t, dense_k=0)):
         ids, cnt, _ = gpu_scan(t, text, cfg=c)
@@ -237,7 +243,7 @@ def test_deep_level(seed, alphabet, npat, lo, hi, deep_k):
     data, off = W.concat(pieces)
     bw = W.Workload("deep_batch", seed, wl.patterns, data, off)
     b_ids, b_counts, _ = ot.scan_batch(data, off)
-    for c in (None, small_cfg(t), dict(cfg, deep=0)):
+    for c in (None, small_cfg(t), no_deep(cfg)):
         ids, counts = batch_gpu(t, bw, c)
         assert np.array_equal(ids, b_ids) and np.array_equal(counts, b_counts)
 
@@ -254,7 +260,7 @@ def test_light_form_equals_persistent(seed, alphabet, npat, lo, hi, n):
     wl = W.random_case(seed, npat, n, alphabet, lo, hi, plant_rate=0.05)
     t = pm.pm_build(wl.patterns)
     o_ids, o_cnt, o_look = oracle.Trie(wl.patterns).scan(wl.text)
-    for cfg in (light(t), persistent(t), light(t, checked=1), light(t, deep=0)
+    for cfg in (light(t), persistent(t), light(t, checked=1), no_deep(light(t))
                 if pm.pm_stats(t)["deep_k"] else light(t, row_search=1), light(t, layout=1)):
         ids, cnt, _ = gpu_scan(t, wl.text, cfg=cfg)
         assert_same(ids, cnt, o_ids, o_cnt)
@@ -469,7 +475,7 @@ def test_truncated_levels_settle_positions():
         matched = int((o_ids >= 0).sum())
         assert matched <= walks <= frac * len(wl.text)
         if pm.pm_stats(t)["deep_k"]:
-            ids0, cnt0, walks0 = walks_of(t, wl.text, cfg=dict(pm.pm_get_config(t), deep=0))
+            ids0, cnt0, walks0 = walks_of(t, wl.text, cfg=no_deep(pm.pm_get_config(t)))
             assert_same(ids0, cnt0, o_ids, o_cnt)
             assert walks0 > 5 * walks       # the filter alone passes several times as many
 
