@@ -36,7 +36,7 @@ def _lib():
 
 
 def dev(a, dtype=torch.uint8):
-    t = torch.from_numpy(np.ascontiguousarray(a))
+    t = torch.from_numpy(np.array(a, copy=True))  # a writable copy
     return t.to("cuda")
 
 
